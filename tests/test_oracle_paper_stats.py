@@ -1,0 +1,72 @@
+"""Statistical pins of the oracle to the numbers printed in the paper.
+
+Table II (Appendix A): BB [[144,12,12]], code capacity, p = 0.01, 1e8 shots:
+13,769 first-BP failures and 2,456 + 500 = 2,956 BP+DC failures.
+Table III (Appendix B): fraction of rows of H_X with posterior spread
+Delta <= eps on first-BP failures.
+
+The paper does not state its min-sum scale factor.  These tables are
+reproduced with plain min-sum (alpha = 1), T_iter = n = 144 (Fig. 2 caption)
+and second-BP priors p (Sec. III.B); alpha = 0.625 gives ~10x more first-BP
+failures, so the pins below also fix that reading for the paper's runs.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import bpdc_inputs as bi
+from bpdc_inputs.sampler import sample_shots
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SHOTS = 1_000_000
+
+
+def _row(fname, code):
+    with open(os.path.join(GOLDEN, fname)) as f:
+        for line in f:
+            t = line.split()
+            if t and t[0] == code:
+                return [float(x) for x in t[1:]]
+    raise KeyError(code)
+
+
+@pytest.fixture(scope="module")
+def bb144_run(oracle_mod):
+    P = bi.bb_problem("bb144", 0.01)
+    _, s, o = sample_shots(P, 0x2510086950 + 100, 0, SHOTS)
+    idx = np.nonzero(s.any(1))[0]          # zero syndromes converge at iteration 0
+    opts = oracle_mod.Options(alpha=1.0, max_iter=144)
+    out = oracle_mod.decode_batch(P, s[idx], 0, opts, want_post1=True)
+    return P, out, o[idx]
+
+
+@pytest.mark.slow
+def test_table2_first_bp_and_bpdc_failure_counts(bb144_run):
+    P, out, obs = bb144_run
+    shots, bp_failed, _, both_fail, _, osd_only = _row("table2_overlap.txt", "bb144")
+    st = out["status"]
+    n_bp = int((st > 0).sum())
+    n_dc = int(((st == 2) | (out["obs_pred"] != obs).any(1)).sum())
+    exp_bp = bp_failed / shots * SHOTS
+    exp_dc = (both_fail + osd_only) / shots * SHOTS
+    # Poisson counts: accept 4 sigma
+    assert abs(n_bp - exp_bp) < 4 * np.sqrt(exp_bp), (n_bp, exp_bp)
+    assert abs(n_dc - exp_dc) < 4 * np.sqrt(exp_dc), (n_dc, exp_dc)
+    # DC rescues most first-BP failures on this code (Table II: 10,813 of 13,769)
+    assert n_dc < 0.5 * n_bp
+
+
+@pytest.mark.slow
+def test_table3_flatness_fractions(bb144_run):
+    P, out, _ = bb144_run
+    expect = _row("table3_flatness.txt", "bb144")
+    failed = out["status"] > 0
+    with np.errstate(over="ignore"):
+        ph = 1.0 / (1.0 + np.exp(out["post1"][failed]))
+    D = P.D.toarray().astype(bool)
+    deltas = np.concatenate([[ph[b, r].max() - ph[b, r].min() for r in D]
+                             for b in range(ph.shape[0])])
+    for eps, pct in zip((0.1, 0.2, 0.3, 0.4, 0.5), expect):
+        got = 100.0 * (deltas <= eps).mean()
+        assert abs(got - pct) < 5.0, (eps, got, pct)
