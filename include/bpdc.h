@@ -1,0 +1,210 @@
+/*
+ * bpdc.h -- C-ABI of the GB300 BP+DC decoder (libbpdc.so).
+ *
+ * Decodes batches of syndrome shots of one decoding problem (H, L, D, p):
+ *   H  (M x N)  matrix whose Tanner graph BP runs on: H_Z under code-capacity
+ *               noise, the detector check matrix H_DCM otherwise
+ *               (arXiv 2510.08695, Sec. II.C and Sec. IV.A);
+ *   L  (K x N)  logical operator matrix O_Z / O, used for the logical flips
+ *               e_hat L^T and the failure test (Sec. II.C, Sec. IV.A);
+ *   D  (Md x N) degeneracy matrix H_X / H_DDM whose rows degeneracy cutting
+ *               acts on (Algorithm 1, Sec. III.A; Sec. IV.B);
+ *   p  (N)      prior error probabilities (Eq. 8).
+ *
+ * The decoder runs flooding normalized min-sum BP (Sec. II.C.1) with FP32
+ * messages.  When BP does not reproduce the syndrome within T_iter
+ * iterations it cuts, for every row of D, the support variable with the
+ * highest posterior LLR (lowest error probability), and runs BP once more on
+ * the cut graph with the original priors (Algorithm 1 with the Sec. III.B
+ * choice of priors; the cut is applied as in Algorithm 2).
+ *
+ * Conventions shared by every call:
+ *   - Every function returns BPDC_OK (0) or a negative BPDC_ERR_* code and
+ *     never aborts the process; bpdc_last_error() gives a message (per
+ *     thread).
+ *   - Bit vectors are packed little-endian into uint32 words: bit (c % 32) of
+ *     word (c / 32) holds entry c.  A shot of a vector of length n takes
+ *     ceil(n/32) words; shot b starts at word b * ceil(n/32).
+ *   - Device pointers are CUDA device (or managed) addresses on the graph's
+ *     device; the caller owns them.  Host pointers are plain host memory.
+ *   - Calls taking a stream (cudaStream_t passed as void*, NULL = legacy
+ *     default stream) are asynchronous: they only enqueue work.  Argument
+ *     errors are reported synchronously; errors raised on the device are
+ *     latched in the graph and returned by bpdc_graph_sync_status().
+ *   - A graph object may be used from one host thread at a time.  Decode
+ *     calls on one graph that run concurrently on different streams are
+ *     allowed: each call uses its own slot of the graph's work counters
+ *     (at most BPDC_MAX_INFLIGHT calls per graph may be in flight).
+ */
+#ifndef BPDC_H
+#define BPDC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BPDC_OK 0
+#define BPDC_ERR_INVALID_ARG (-1)   /* a null, out-of-range or inconsistent argument */
+#define BPDC_ERR_DIM_MISMATCH (-2)  /* matrix shapes disagree */
+#define BPDC_ERR_OOM (-3)           /* device or host allocation failed */
+#define BPDC_ERR_CUDA (-4)          /* a CUDA runtime call failed */
+#define BPDC_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
+#define BPDC_ERR_UNSUPPORTED (-6)   /* valid request the library does not implement */
+
+#define BPDC_MAX_INFLIGHT 64
+
+typedef struct bpdc_graph_s *bpdc_graph_t;
+
+/* A 0/1 matrix in CSR form (host memory).  row_ptr has rows+1 entries with
+ * row_ptr[0] = 0 and row_ptr[rows] = nnz; col_idx has nnz entries in
+ * [0, cols).  Duplicate entries within a row are rejected. */
+typedef struct {
+    int32_t rows, cols;
+    int64_t nnz;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+} bpdc_csr;
+
+/* Decoding options, fixed when the graph is created. */
+typedef struct {
+    int32_t variant;   /* 0: normalized min-sum (the only one implemented) */
+    float ms_scale;    /* alpha, the min-sum scale factor, in (0, 1] */
+    int32_t max_iter;  /* T_iter, the BP iteration limit of each run, 0..65535 */
+    int32_t dc_enable; /* 1: degeneracy cutting on BP failure; 0: plain BP */
+    int32_t dc_prior;  /* 0: second BP on the priors p (Sec. III.B, BB codes);
+                          1: on the first-run posterior p_hat clamped to
+                          [1e-12, 1/2] (Algorithm 1 as printed) */
+    float tie_rel;     /* tie window of the cut selection (>= 0): candidates of a
+                          row are the variables with
+                          L_j >= L_max - tie_rel * max(1, |L_max|) */
+    uint64_t tie_seed; /* key of the SplitMix64 tie-break hash: the candidate of
+                          rank h(tie_seed, shot * Md + row) mod |candidates|
+                          (ascending column order) is cut */
+} bpdc_opts;
+
+/* Fills *o with the defaults: min-sum, alpha = 0.625, T_iter = 50, DC on,
+ * priors p, tie_rel = 1e-5, tie_seed = 0x2510086950. */
+void bpdc_opts_default(bpdc_opts *o);
+
+/* Builds a device-resident decoding problem on CUDA device `device`.
+ * H: M x N check matrix (every column must have at least one entry is not
+ * required; empty columns are allowed).  L: K x N (K may be 0, rows may be
+ * empty).  D: Md x N (Md may be 0; empty rows are skipped by the cut).
+ * priors: N host doubles in (0, 1/2].  The library copies everything; the
+ * caller may free its arrays on return.  Limits: N, M <= 65535, row weight of
+ * H <= 16, column weight of H <= 8, row weight of D <= 64.
+ * Errors: INVALID_ARG (null pointer, malformed CSR, prior outside (0, 1/2],
+ * option out of range), DIM_MISMATCH (column counts differ),
+ * UNSUPPORTED (a limit above is exceeded), OOM, CUDA. */
+int bpdc_graph_create(const bpdc_csr *H, const bpdc_csr *L, const bpdc_csr *D,
+                      const double *priors, const bpdc_opts *opts, int device,
+                      bpdc_graph_t *out);
+
+/* Frees the graph and its device memory.  Waits for no stream: the caller
+ * must make sure no decode call on the graph is still running.  NULL is a
+ * no-op. */
+int bpdc_graph_destroy(bpdc_graph_t g);
+
+/* Sizes and the chosen launch plan of a graph. */
+typedef struct {
+    int32_t M, N, K, Md;
+    int64_t E;                  /* nnz(H) = edges of the Tanner graph */
+    int32_t syndrome_words;     /* ceil(M/32) */
+    int32_t correction_words;   /* ceil(N/32) */
+    int32_t logical_words;      /* ceil(K/32) */
+    int32_t threads_per_shot;   /* G: threads that decode one shot together */
+    int32_t shots_per_block;    /* groups of G threads per CTA */
+    int32_t blocks_per_sm;      /* resident CTAs per SM of the persistent form */
+    int32_t smem_per_block;     /* dynamic shared memory of one CTA, bytes */
+    int32_t kernel_id;          /* index of the compiled kernel variant */
+} bpdc_graph_info;
+
+int bpdc_graph_get_info(bpdc_graph_t g, bpdc_graph_info *info);
+
+/* Replaces the launch plan: threads_per_shot G in {4, 8, 16, 32, 64, 128,
+ * 256, 512} (0 = automatic).  Used by the autotuner.  UNSUPPORTED if no
+ * compiled kernel variant fits the graph with that G. */
+int bpdc_graph_set_plan(bpdc_graph_t g, int32_t threads_per_shot);
+
+/* Outputs of a decode call (device pointers; NULL where optional). */
+typedef struct {
+    uint32_t *corrections;       /* required: [B][ceil(N/32)] e_hat bits (cut variables 0) */
+    uint8_t *status;             /* required: [B] 0 BP converged, 1 BP+DC converged, 2 failure */
+    uint32_t *logical_flips;     /* optional: [B][ceil(K/32)] bits of e_hat L^T */
+    const uint32_t *obs_true;    /* optional input: [B][ceil(K/32)] bits of e L^T of the true
+                                    error; with it a shot fails if status == 2 or the
+                                    logical flips differ */
+    uint32_t *iterations;        /* optional: [B] BP iterations, first run in bits 0-15,
+                                    second run in bits 16-31 */
+    float *posterior_llr;        /* optional: [B][N] final posterior LLRs (cut variables
+                                    +inf); slower path */
+    unsigned long long *counters;/* optional: [4] accumulated (atomically added) over the
+                                    call: shots, failures (needs obs_true; else status 2),
+                                    BP iterations run (both runs), shots that ran DC */
+    const uint32_t *cut_in;      /* optional input: [B][ceil(N/32)] a cut set per shot.  With
+                                    it the call runs one BP on the cut graph (Algorithm 2
+                                    form) and no DC: status 0 converged, 2 not */
+} bpdc_outputs;
+
+/* Decodes B >= 0 shots.  syndromes: device [B][ceil(M/32)].  Shot b has the
+ * global index shot_offset + b, which keys the tie-break hash, so results do
+ * not depend on how shots are split across calls or GPUs.  persistent = 1
+ * launches one resident grid that pulls shots from a device work counter;
+ * persistent = 0 launches the plain per-batch grid (one group per shot).
+ * Both give identical results.  Asynchronous on `stream`. */
+int bpdc_decode(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, uint64_t shot_offset,
+                const bpdc_outputs *out, int persistent, void *stream);
+
+/* One item of a multi-problem launch. */
+typedef struct {
+    bpdc_graph_t graph;
+    int64_t B;
+    const uint32_t *syndromes;
+    uint64_t shot_offset;
+    bpdc_outputs out;
+} bpdc_batch;
+
+/* Decodes several batches, possibly of different graphs, in as few persistent
+ * launches as the compiled kernel variants allow (one per variant), with the
+ * shots of all batches of a variant behind one device work counter.  All
+ * graphs must live on the same device; results equal those of bpdc_decode
+ * on each batch.  Asynchronous on `stream`. */
+int bpdc_decode_multi(const bpdc_batch *batches, int32_t n_batches, void *stream);
+
+/* Cut selection alone (lines 4-7 of Algorithm 1) from given posterior LLRs:
+ * posterior_llr device [B][N] floats, cut_out device [B][ceil(N/32)] bits.
+ * Uses the graph's D, tie_rel and tie_seed. */
+int bpdc_cut_select(bpdc_graph_t g, int64_t B, const float *posterior_llr, uint64_t shot_offset,
+                    uint32_t *cut_out, void *stream);
+
+/* Seeded shot sampler (benchmark inputs): e_ij = [(h(seed, i*N + j) >> 32) <
+ * floor(p_j * 2^32)] for global shot i = shot_offset + b, h the SplitMix64
+ * output function; writes syndromes e H^T [B][ceil(M/32)] and, if non-NULL,
+ * observables e L^T [B][ceil(K/32)] and errors [B][ceil(N/32)]. */
+int bpdc_sample(bpdc_graph_t g, int64_t B, uint64_t seed, uint64_t shot_offset,
+                uint32_t *syndromes, uint32_t *observables, uint32_t *errors, void *stream);
+
+/* Waits for the graph's device work on `stream` and returns the first device
+ * error latched since the last call (BPDC_ERR_TIMEOUT, BPDC_ERR_CUDA), then
+ * clears it. */
+int bpdc_graph_sync_status(bpdc_graph_t g, void *stream);
+
+/* Gradient of a weighted-BP loss (differentiable weighted BP).  Not
+ * implemented: always returns BPDC_ERR_UNSUPPORTED. */
+int bpdc_decode_backward(bpdc_graph_t g, int64_t B, const uint32_t *syndromes,
+                         const float *weights, const float *grad_llr, float *grad_weights,
+                         void *stream);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *bpdc_last_error(void);
+
+/* Library version string. */
+const char *bpdc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPDC_H */

@@ -1,0 +1,6 @@
+"""GB300-native BP+DC decoder (arXiv 2510.08695): batched flooding min-sum BP
+with degeneracy cutting, as hand-written sm_103a CUDA behind the C-ABI of
+``libbpdc.so`` (declared in ``include/bpdc.h``)."""
+from ._bpdc import (  # noqa: F401
+    BpdcError, Graph, Options, decode_multi, declared_symbols, library_path, load, version,
+)

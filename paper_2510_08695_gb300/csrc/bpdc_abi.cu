@@ -1,0 +1,639 @@
+// C-ABI of libbpdc.so: argument validation, Tanner-graph packing for the
+// group-per-shot kernels, launch planning and asynchronous launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/bpdc.h"
+#include "bpdc_internal.h"
+
+using namespace bpdc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(BPDC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes `dev` current for the scope and restores the caller's device.
+struct DeviceGuard {
+    int old = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&old) != cudaSuccess) old = -1;
+        if (old != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (old >= 0) {
+            int cur = -1;
+            if (cudaGetDevice(&cur) == cudaSuccess && cur != old) cudaSetDevice(old);
+        }
+    }
+};
+
+constexpr int kRing = BPDC_MAX_INFLIGHT;
+constexpr int kMaxBatches = 32;
+constexpr int kMaxSmemPerBlock = 227 * 1024;
+
+struct HostCsr {
+    int32_t rows = 0, cols = 0;
+    std::vector<int32_t> ptr, col;
+};
+
+int copy_csr(const bpdc_csr *m, const char *name, HostCsr &out)
+{
+    if (!m) return fail(BPDC_ERR_INVALID_ARG, "%s is NULL", name);
+    if (m->rows < 0 || m->cols < 0 || m->nnz < 0)
+        return fail(BPDC_ERR_INVALID_ARG, "%s has negative dimensions", name);
+    if (!m->row_ptr) return fail(BPDC_ERR_INVALID_ARG, "%s.row_ptr is NULL", name);
+    if (m->nnz > 0 && !m->col_idx) return fail(BPDC_ERR_INVALID_ARG, "%s.col_idx is NULL", name);
+    if (m->row_ptr[0] != 0 || m->row_ptr[m->rows] != m->nnz)
+        return fail(BPDC_ERR_INVALID_ARG, "%s.row_ptr must start at 0 and end at nnz", name);
+    out.rows = m->rows;
+    out.cols = m->cols;
+    out.ptr.assign(m->row_ptr, m->row_ptr + m->rows + 1);
+    out.col.assign(m->col_idx, m->col_idx + m->nnz);
+    for (int32_t r = 0; r < m->rows; ++r) {
+        if (out.ptr[r + 1] < out.ptr[r]) return fail(BPDC_ERR_INVALID_ARG, "%s.row_ptr decreases at row %d", name, r);
+        std::sort(out.col.begin() + out.ptr[r], out.col.begin() + out.ptr[r + 1]);
+        for (int32_t a = out.ptr[r]; a < out.ptr[r + 1]; ++a) {
+            if (out.col[a] < 0 || out.col[a] >= m->cols)
+                return fail(BPDC_ERR_INVALID_ARG, "%s: column %d out of range in row %d", name, out.col[a], r);
+            if (a > out.ptr[r] && out.col[a] == out.col[a - 1])
+                return fail(BPDC_ERR_INVALID_ARG, "%s: duplicate column %d in row %d", name, out.col[a], r);
+        }
+    }
+    return BPDC_OK;
+}
+
+struct RingSlot {
+    BatchDesc *dev_desc = nullptr;       // kMaxBatches descriptors
+    BatchDesc *host_desc = nullptr;      // pinned mirror
+    unsigned long long *work = nullptr;  // persistent work counter
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+
+}  // namespace
+
+struct bpdc_graph_s {
+    int device = 0;
+    int sm_count = 0;
+    bpdc_opts opts{};
+    HostCsr H, L, D;
+    std::vector<double> priors;
+    DevGraph dg{};
+    void *arena = nullptr;
+    int variant = -1;
+    int groups_per_block = 0;
+    int blocks_per_sm = 0;
+    int smem_bytes = 0;
+    int regs = 0;
+    void *ring_mem = nullptr;
+    void *ring_host = nullptr;
+    RingSlot ring[kRing];
+    int ring_next = 0;
+    std::mutex mu;
+};
+
+namespace {
+
+// Message-slot layout of the packing: variable j at lane j % G, pass j / G,
+// its m-th edge (ascending check index) in slot ((j/G)*cv + m)*G + j%G.
+struct Packed {
+    int G, pc, pv, dc, cv, slots, cmw, region, KW, NW, MW;
+    std::vector<uint16_t> chk_idx;
+    std::vector<uint8_t> var_deg;
+    std::vector<float> lam;
+    std::vector<int32_t> d_ptr;
+    std::vector<uint32_t> d_ent;
+    std::vector<uint32_t> l_cols;
+    std::vector<uint32_t> thr;
+};
+
+int pack(const bpdc_graph_s &g, int G, Packed &P)
+{
+    const int M = g.H.rows, N = g.H.cols, K = g.L.rows, Md = g.D.rows;
+    P.G = G;
+    P.pc = std::max(1, (M + G - 1) / G);
+    P.pv = std::max(1, (N + G - 1) / G);
+    std::vector<int> deg(N, 0);
+    int dc = 0;
+    for (int i = 0; i < M; ++i) dc = std::max(dc, g.H.ptr[i + 1] - g.H.ptr[i]);
+    for (int32_t c : g.H.col) deg[c]++;
+    int cv = 1;
+    for (int j = 0; j < N; ++j) cv = std::max(cv, deg[j]);
+    P.dc = std::max(dc, 1);
+    P.cv = cv;
+    const long slots = (long)P.pv * P.cv * G;
+    if (slots > 65535) return fail(BPDC_ERR_UNSUPPORTED, "graph needs %ld message slots per shot (max 65535)", slots);
+    P.slots = (int)slots;
+    P.cmw = (P.pv * G + 31) / 32;
+    P.NW = (N + 31) / 32;
+    P.MW = (M + 31) / 32;
+    P.KW = (K + 31) / 32;
+    int region = 2 + P.slots + P.cmw + std::max(P.KW, 1);
+    if (G < 32) {
+        while (region % 32 != G % 32) ++region;   // spread the groups of a warp over the banks
+    } else {
+        region = (region + 3) & ~3;
+    }
+    P.region = region;
+    // edge -> slot
+    std::vector<int> fill(N, 0);
+    std::vector<int> edge_slot(g.H.col.size());
+    for (int i = 0; i < M; ++i)
+        for (int a = g.H.ptr[i]; a < g.H.ptr[i + 1]; ++a) {
+            const int j = g.H.col[a];
+            const int m = fill[j]++;
+            edge_slot[a] = ((j / G) * P.cv + m) * G + (j % G);
+        }
+    P.chk_idx.assign((size_t)P.pc * P.dc * G, kNoEdge);
+    for (int i = 0; i < M; ++i) {
+        const int p = i / G, u = i % G;
+        for (int a = g.H.ptr[i], k = 0; a < g.H.ptr[i + 1]; ++a, ++k)
+            P.chk_idx[((size_t)p * P.dc + k) * G + u] = (uint16_t)edge_slot[a];
+    }
+    P.var_deg.assign((size_t)P.pv * G, 0);
+    P.lam.assign((size_t)P.pv * G, 0.0f);
+    for (int j = 0; j < N; ++j) {
+        P.var_deg[j] = (uint8_t)deg[j];   // position p*G+u == j
+        P.lam[j] = (float)std::log((1.0 - g.priors[j]) / g.priors[j]);
+    }
+    P.d_ptr.assign(Md + 1, 0);
+    P.d_ent.clear();
+    for (int r = 0; r < Md; ++r) {
+        for (int a = g.D.ptr[r]; a < g.D.ptr[r + 1]; ++a) {
+            const int j = g.D.col[a];
+            const uint32_t s0 = (uint32_t)(((j / G) * P.cv) * G + (j % G));
+            P.d_ent.push_back(s0 | ((uint32_t)j << 16));
+        }
+        P.d_ptr[r + 1] = (int32_t)P.d_ent.size();
+    }
+    P.l_cols.assign((size_t)N * std::max(P.KW, 1), 0);
+    for (int k = 0; k < K; ++k)
+        for (int a = g.L.ptr[k]; a < g.L.ptr[k + 1]; ++a)
+            P.l_cols[(size_t)g.L.col[a] * P.KW + (k >> 5)] |= 1u << (k & 31);
+    P.thr.resize(N);
+    for (int j = 0; j < N; ++j) P.thr[j] = (uint32_t)std::floor(g.priors[j] * 4294967296.0);
+    return BPDC_OK;
+}
+
+bool variant_fits(int id, const Packed &P)
+{
+    const Variant &v = variant(id);
+    if (v.G != P.G || P.pc > v.pc_max || P.dc > v.dc_max || P.pv > v.pv_max || P.cv > v.cv_max) return false;
+    const long smem = (long)(v.block_threads / v.G) * P.region * 4;
+    return smem <= kMaxSmemPerBlock;
+}
+
+template <typename T>
+size_t put(std::vector<char> &blob, const std::vector<T> &v)
+{
+    size_t off = (blob.size() + 255) & ~(size_t)255;
+    blob.resize(off + std::max<size_t>(v.size() * sizeof(T), 4), 0);
+    if (!v.empty()) memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+}
+
+// Packs the graph for threads_per_shot G (0 = automatic) and uploads it.
+int plan_and_upload(bpdc_graph_s *g, int want_G)
+{
+    static const int kAutoG[] = {8, 16, 32, 4, 256, 128, 512};
+    Packed P{};
+    int vid = -1;
+    std::vector<int> candidates;
+    if (want_G) candidates.push_back(want_G);
+    else candidates.assign(std::begin(kAutoG), std::end(kAutoG));
+    int last_err = BPDC_OK;
+    for (int G : candidates) {
+        Packed Q{};
+        int rc = pack(*g, G, Q);
+        if (rc != BPDC_OK) { last_err = rc; continue; }
+        for (int id = 0; id < num_variants(); ++id)
+            if (variant_fits(id, Q)) { vid = id; break; }
+        if (vid >= 0) { P = std::move(Q); break; }
+    }
+    if (vid < 0) {
+        if (last_err != BPDC_OK && want_G) return last_err;
+        return fail(BPDC_ERR_UNSUPPORTED, "no compiled kernel variant fits this graph%s",
+                    want_G ? " with the requested threads per shot" : "");
+    }
+    const Variant &v = variant(vid);
+    const int gpb = v.block_threads / v.G;
+    const int smem = gpb * P.region * 4;
+    int bps = 0, regs = 0;
+    cudaError_t e = variant_attributes(vid, smem, &bps, &regs);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    if (bps < 1) return fail(BPDC_ERR_UNSUPPORTED, "kernel variant %d cannot be resident with %d bytes of shared memory", vid, smem);
+
+    // device arena
+    std::vector<char> blob;
+    const size_t o_chk = put(blob, P.chk_idx), o_deg = put(blob, P.var_deg), o_lam = put(blob, P.lam);
+    const size_t o_dptr = put(blob, P.d_ptr), o_dent = put(blob, P.d_ent), o_l = put(blob, P.l_cols);
+    const size_t o_hptr = put(blob, g->H.ptr), o_hcol = put(blob, g->H.col), o_thr = put(blob, P.thr);
+    const size_t o_err = put(blob, std::vector<int32_t>(4, 0));
+    void *arena = nullptr;
+    e = cudaMalloc(&arena, blob.size());
+    if (e != cudaSuccess) return fail(BPDC_ERR_OOM, "cudaMalloc of %zu bytes: %s", blob.size(), cudaGetErrorString(e));
+    e = cudaMemcpy(arena, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(arena); return cuda_fail(e, "upload of the graph"); }
+    if (g->arena) cudaFree(g->arena);
+    g->arena = arena;
+    char *base = (char *)arena;
+    DevGraph &d = g->dg;
+    d.M = g->H.rows; d.N = g->H.cols; d.K = g->L.rows; d.Md = g->D.rows;
+    d.MW = P.MW; d.NW = P.NW; d.KW = P.KW;
+    d.G = P.G; d.pc = P.pc; d.pv = P.pv; d.dc = P.dc; d.cv = P.cv;
+    d.slots = P.slots; d.cmw = P.cmw; d.region = P.region;
+    d.max_iter = g->opts.max_iter;
+    d.alpha = g->opts.ms_scale;
+    d.tie_rel = g->opts.tie_rel;
+    d.tie_seed = g->opts.tie_seed;
+    d.dc_enable = g->opts.dc_enable;
+    d.dc_prior = g->opts.dc_prior;
+    d.zero_ok = 1;
+    for (double p : g->priors) if (!(p < 0.5)) d.zero_ok = 0;
+    d.kernel_id = vid;
+    d.chk_idx = (const uint16_t *)(base + o_chk);
+    d.var_deg = (const uint8_t *)(base + o_deg);
+    d.lam = (const float *)(base + o_lam);
+    d.d_ptr = (const int32_t *)(base + o_dptr);
+    d.d_ent = (const uint32_t *)(base + o_dent);
+    d.l_bits = (const uint32_t *)(base + o_l);
+    d.h_ptr = (const int32_t *)(base + o_hptr);
+    d.h_col = (const int32_t *)(base + o_hcol);
+    d.thr = (const uint32_t *)(base + o_thr);
+    d.err_flag = (int32_t *)(base + o_err);
+    g->variant = vid;
+    g->groups_per_block = gpb;
+    g->blocks_per_sm = bps;
+    g->smem_bytes = smem;
+    g->regs = regs;
+    return BPDC_OK;
+}
+
+int ring_init(bpdc_graph_s *g)
+{
+    const size_t per = sizeof(BatchDesc) * kMaxBatches + 256;
+    cudaError_t e = cudaMalloc(&g->ring_mem, per * kRing);
+    if (e != cudaSuccess) return fail(BPDC_ERR_OOM, "ring allocation: %s", cudaGetErrorString(e));
+    e = cudaMallocHost(&g->ring_host, sizeof(BatchDesc) * kMaxBatches * kRing);
+    if (e != cudaSuccess) return fail(BPDC_ERR_OOM, "pinned ring allocation: %s", cudaGetErrorString(e));
+    for (int s = 0; s < kRing; ++s) {
+        char *b = (char *)g->ring_mem + per * s;
+        g->ring[s].work = (unsigned long long *)b;
+        g->ring[s].dev_desc = (BatchDesc *)(b + 256);
+        g->ring[s].host_desc = (BatchDesc *)g->ring_host + (size_t)kMaxBatches * s;
+        e = cudaEventCreateWithFlags(&g->ring[s].done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "event creation");
+    }
+    return BPDC_OK;
+}
+
+void graph_free(bpdc_graph_s *g)
+{
+    for (int s = 0; s < kRing; ++s)
+        if (g->ring[s].done) cudaEventDestroy(g->ring[s].done);
+    if (g->ring_mem) cudaFree(g->ring_mem);
+    if (g->ring_host) cudaFreeHost(g->ring_host);
+    if (g->arena) cudaFree(g->arena);
+    delete g;
+}
+
+int check_outputs(const bpdc_outputs *o)
+{
+    if (!o) return fail(BPDC_ERR_INVALID_ARG, "outputs is NULL");
+    if (!o->corrections) return fail(BPDC_ERR_INVALID_ARG, "outputs.corrections is NULL");
+    if (!o->status) return fail(BPDC_ERR_INVALID_ARG, "outputs.status is NULL");
+    return BPDC_OK;
+}
+
+void fill_desc(BatchDesc &d, const bpdc_graph_s *g, int64_t B, const uint32_t *syn, uint64_t off,
+               const bpdc_outputs *o, int64_t first)
+{
+    d.g = g->dg;
+    d.B = B;
+    d.first = first;
+    d.syn = syn;
+    d.shot_offset = off;
+    d.corr = o->corrections;
+    d.status = o->status;
+    d.lflips = o->logical_flips;
+    d.obs_true = o->obs_true;
+    d.iters = o->iterations;
+    d.post = o->posterior_llr;
+    d.counters = o->counters;
+    d.cut_in = o->cut_in;
+}
+
+// Enqueues one launch of variant `vid` over n descriptors (already filled in
+// the host mirror of ring slot s).
+int enqueue(bpdc_graph_s *g, int s, int n, int64_t total, int vid, int smem, bool persistent,
+            cudaStream_t stream)
+{
+    RingSlot &rs = g->ring[s];
+    cudaError_t e = cudaMemcpyAsync(rs.dev_desc, rs.host_desc, sizeof(BatchDesc) * n,
+                                    cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "descriptor upload");
+    LaunchDesc ld{};
+    ld.batches = rs.dev_desc;
+    ld.n_batches = n;
+    ld.total = total;
+    ld.work = nullptr;
+    const Variant &v = variant(vid);
+    const int gpb = v.block_threads / v.G;
+    int bps = 0, regs = 0;
+    e = variant_attributes(vid, smem, &bps, &regs);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    if (bps < 1) return fail(BPDC_ERR_UNSUPPORTED, "kernel variant %d not resident with %d bytes", vid, smem);
+    int64_t grid;
+    const int64_t need = (total + gpb - 1) / gpb;
+    if (persistent) {
+        e = cudaMemsetAsync(rs.work, 0, sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "work counter reset");
+        ld.work = (unsigned int *)rs.work;
+        grid = std::min<int64_t>((int64_t)g->sm_count * bps, need);
+    } else {
+        grid = need;
+    }
+    if (grid > 0x7FFFFFFF) return fail(BPDC_ERR_UNSUPPORTED, "batch too large for one launch");
+    e = launch_variant(vid, ld, (int)grid, smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    e = cudaEventRecord(rs.done, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "event record");
+    rs.used = true;
+    return BPDC_OK;
+}
+
+int acquire_slot(bpdc_graph_s *g)
+{
+    const int s = g->ring_next;
+    g->ring_next = (g->ring_next + 1) % kRing;
+    if (g->ring[s].used) cudaEventSynchronize(g->ring[s].done);
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bpdc_opts_default(bpdc_opts *o)
+{
+    if (!o) return;
+    o->variant = 0;
+    o->ms_scale = 0.625f;
+    o->max_iter = 50;
+    o->dc_enable = 1;
+    o->dc_prior = 0;
+    o->tie_rel = 1e-5f;
+    o->tie_seed = 0x2510086950ull;
+}
+
+const char *bpdc_last_error(void) { return g_last_error.c_str(); }
+
+const char *bpdc_version(void) { return "bpdc 0.1 (sm_103a)"; }
+
+int bpdc_graph_create(const bpdc_csr *H, const bpdc_csr *L, const bpdc_csr *D, const double *priors,
+                      const bpdc_opts *opts, int device, bpdc_graph_t *out)
+{
+    g_last_error.clear();
+    if (!out) return fail(BPDC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!priors) return fail(BPDC_ERR_INVALID_ARG, "priors is NULL");
+    bpdc_opts o;
+    if (opts) o = *opts; else bpdc_opts_default(&o);
+    if (o.variant != 0) return fail(BPDC_ERR_UNSUPPORTED, "only the min-sum variant (0) is implemented");
+    if (!(o.ms_scale > 0.0f && o.ms_scale <= 1.0f)) return fail(BPDC_ERR_INVALID_ARG, "ms_scale must be in (0, 1]");
+    if (o.max_iter < 0 || o.max_iter > 65535) return fail(BPDC_ERR_INVALID_ARG, "max_iter must be in [0, 65535]");
+    if ((o.dc_enable != 0 && o.dc_enable != 1) || (o.dc_prior != 0 && o.dc_prior != 1))
+        return fail(BPDC_ERR_INVALID_ARG, "dc_enable and dc_prior must be 0 or 1");
+    if (!(o.tie_rel >= 0.0f) || !std::isfinite(o.tie_rel)) return fail(BPDC_ERR_INVALID_ARG, "tie_rel must be finite and >= 0");
+    auto *g = new (std::nothrow) bpdc_graph_s();
+    if (!g) return fail(BPDC_ERR_OOM, "host allocation");
+    g->opts = o;
+    g->device = device;
+    int rc;
+    if ((rc = copy_csr(H, "H", g->H)) != BPDC_OK || (rc = copy_csr(L, "L", g->L)) != BPDC_OK ||
+        (rc = copy_csr(D, "D", g->D)) != BPDC_OK) {
+        delete g;
+        return rc;
+    }
+    const int N = g->H.cols;
+    if (g->L.cols != N || g->D.cols != N) {
+        delete g;
+        return fail(BPDC_ERR_DIM_MISMATCH, "H, L and D must have the same number of columns (%d, %d, %d)", N,
+                    g->L.cols, g->D.cols);
+    }
+    if (N > 65535 || g->H.rows > 65535) {
+        delete g;
+        return fail(BPDC_ERR_UNSUPPORTED, "at most 65535 variables and checks");
+    }
+    for (int r = 0; r < g->D.rows; ++r)
+        if (g->D.ptr[r + 1] - g->D.ptr[r] > kMaxDRowWeight) {
+            delete g;
+            return fail(BPDC_ERR_UNSUPPORTED, "row %d of D has weight above %d", r, kMaxDRowWeight);
+        }
+    g->priors.assign(priors, priors + N);
+    for (int j = 0; j < N; ++j)
+        if (!(g->priors[j] > 0.0 && g->priors[j] <= 0.5)) {
+            delete g;
+            return fail(BPDC_ERR_INVALID_ARG, "prior %d = %g outside (0, 1/2]", j, g->priors[j]);
+        }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaGetDeviceCount"); }
+    if (device < 0 || device >= ndev) { delete g; return fail(BPDC_ERR_INVALID_ARG, "device %d does not exist", device); }
+    DeviceGuard dgd(device);
+    if (!dgd.ok) { delete g; return fail(BPDC_ERR_CUDA, "cannot select device %d", device); }
+    e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "SM count"); }
+    if ((rc = plan_and_upload(g, 0)) != BPDC_OK || (rc = ring_init(g)) != BPDC_OK) {
+        graph_free(g);
+        return rc;
+    }
+    *out = g;
+    return BPDC_OK;
+}
+
+int bpdc_graph_destroy(bpdc_graph_t g)
+{
+    if (!g) return BPDC_OK;
+    DeviceGuard dgd(g->device);
+    graph_free(g);
+    return BPDC_OK;
+}
+
+int bpdc_graph_get_info(bpdc_graph_t g, bpdc_graph_info *info)
+{
+    if (!g || !info) return fail(BPDC_ERR_INVALID_ARG, "NULL argument");
+    info->M = g->dg.M; info->N = g->dg.N; info->K = g->dg.K; info->Md = g->dg.Md;
+    info->E = (int64_t)g->H.col.size();
+    info->syndrome_words = g->dg.MW;
+    info->correction_words = g->dg.NW;
+    info->logical_words = g->dg.KW;
+    info->threads_per_shot = g->dg.G;
+    info->shots_per_block = g->groups_per_block;
+    info->blocks_per_sm = g->blocks_per_sm;
+    info->smem_per_block = g->smem_bytes;
+    info->kernel_id = g->variant;
+    return BPDC_OK;
+}
+
+int bpdc_graph_set_plan(bpdc_graph_t g, int32_t threads_per_shot)
+{
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    static const int ok[] = {0, 4, 8, 16, 32, 64, 128, 256, 512};
+    if (std::find(std::begin(ok), std::end(ok), threads_per_shot) == std::end(ok))
+        return fail(BPDC_ERR_INVALID_ARG, "threads_per_shot %d not in {0,4,...,512}", threads_per_shot);
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dgd(g->device);
+    // wait for launches that still read the old arena
+    for (int s = 0; s < kRing; ++s)
+        if (g->ring[s].used) cudaEventSynchronize(g->ring[s].done);
+    const DevGraph keep = g->dg;
+    void *keep_arena = g->arena;
+    const int kv = g->variant, kg = g->groups_per_block, kb = g->blocks_per_sm, ks = g->smem_bytes;
+    g->arena = nullptr;
+    int rc = plan_and_upload(g, threads_per_shot);
+    if (rc != BPDC_OK) {
+        g->dg = keep; g->arena = keep_arena; g->variant = kv;
+        g->groups_per_block = kg; g->blocks_per_sm = kb; g->smem_bytes = ks;
+        return rc;
+    }
+    cudaFree(keep_arena);
+    return BPDC_OK;
+}
+
+int bpdc_decode(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, uint64_t shot_offset,
+                const bpdc_outputs *out, int persistent, void *stream)
+{
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    if (B < 0) return fail(BPDC_ERR_INVALID_ARG, "B < 0");
+    int rc = check_outputs(out);
+    if (rc != BPDC_OK) return rc;
+    if (B == 0) return BPDC_OK;
+    if (!syndromes) return fail(BPDC_ERR_INVALID_ARG, "syndromes is NULL");
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dgd(g->device);
+    const int s = acquire_slot(g);
+    fill_desc(g->ring[s].host_desc[0], g, B, syndromes, shot_offset, out, 0);
+    return enqueue(g, s, 1, B, g->variant, g->smem_bytes, persistent != 0, (cudaStream_t)stream);
+}
+
+int bpdc_decode_multi(const bpdc_batch *batches, int32_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && !batches)) return fail(BPDC_ERR_INVALID_ARG, "bad batch list");
+    if (n == 0) return BPDC_OK;
+    const int dev = batches[0].graph ? batches[0].graph->device : -1;
+    for (int i = 0; i < n; ++i) {
+        if (!batches[i].graph) return fail(BPDC_ERR_INVALID_ARG, "batch %d has no graph", i);
+        if (batches[i].graph->device != dev) return fail(BPDC_ERR_INVALID_ARG, "graphs on different devices");
+        if (batches[i].B < 0) return fail(BPDC_ERR_INVALID_ARG, "batch %d: B < 0", i);
+        if (batches[i].B > 0 && !batches[i].syndromes) return fail(BPDC_ERR_INVALID_ARG, "batch %d: syndromes NULL", i);
+        int rc = check_outputs(&batches[i].out);
+        if (rc != BPDC_OK) return rc;
+    }
+    bpdc_graph_s *owner = batches[0].graph;
+    std::lock_guard<std::mutex> lk(owner->mu);
+    DeviceGuard dgd(dev);
+    // one launch per kernel variant (chunks of at most kMaxBatches batches)
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return batches[a].graph->variant < batches[b].graph->variant;
+    });
+    size_t i = 0;
+    while (i < order.size()) {
+        const int vid = batches[order[i]].graph->variant;
+        const int s = acquire_slot(owner);
+        int cnt = 0, smem = 0;
+        int64_t total = 0;
+        while (i < order.size() && cnt < kMaxBatches && batches[order[i]].graph->variant == vid) {
+            const bpdc_batch &bt = batches[order[i]];
+            if (bt.B > 0) {
+                fill_desc(owner->ring[s].host_desc[cnt], bt.graph, bt.B, bt.syndromes, bt.shot_offset, &bt.out, total);
+                total += bt.B;
+                smem = std::max(smem, bt.graph->smem_bytes);
+                ++cnt;
+            }
+            ++i;
+        }
+        if (cnt == 0) continue;
+        int rc = enqueue(owner, s, cnt, total, vid, smem, true, (cudaStream_t)stream);
+        if (rc != BPDC_OK) return rc;
+    }
+    return BPDC_OK;
+}
+
+int bpdc_cut_select(bpdc_graph_t g, int64_t B, const float *posterior_llr, uint64_t shot_offset,
+                    uint32_t *cut_out, void *stream)
+{
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    if (B < 0) return fail(BPDC_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return BPDC_OK;
+    if (!posterior_llr || !cut_out) return fail(BPDC_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard dgd(g->device);
+    cudaError_t e = launch_cut_select(g->dg, B, posterior_llr, shot_offset, cut_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? BPDC_OK : cuda_fail(e, "cut-select launch");
+}
+
+int bpdc_sample(bpdc_graph_t g, int64_t B, uint64_t seed, uint64_t shot_offset, uint32_t *syndromes,
+                uint32_t *observables, uint32_t *errors, void *stream)
+{
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    if (B < 0) return fail(BPDC_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return BPDC_OK;
+    if (!syndromes) return fail(BPDC_ERR_INVALID_ARG, "syndromes is NULL");
+    DeviceGuard dgd(g->device);
+    cudaError_t e = launch_sample(g->dg, B, seed, shot_offset, syndromes, observables, errors, (cudaStream_t)stream);
+    return e == cudaSuccess ? BPDC_OK : cuda_fail(e, "sampler launch");
+}
+
+int bpdc_graph_sync_status(bpdc_graph_t g, void *stream)
+{
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    DeviceGuard dgd(g->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    int32_t flag = 0;
+    e = cudaMemcpy(&flag, g->dg.err_flag, sizeof(flag), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (flag != 0) {
+        const int32_t zero = 0;
+        cudaMemcpy(g->dg.err_flag, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        return fail(flag, "device reported error %d", flag);
+    }
+    return BPDC_OK;
+}
+
+int bpdc_decode_backward(bpdc_graph_t, int64_t, const uint32_t *, const float *, const float *, float *,
+                         void *)
+{
+    return fail(BPDC_ERR_UNSUPPORTED, "bpdc_decode_backward: differentiable weighted BP is not implemented");
+}
+
+}  // extern "C"

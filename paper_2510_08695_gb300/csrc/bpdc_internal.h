@@ -1,0 +1,95 @@
+// Internal declarations shared by the host packing code and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bpdc {
+
+// Check-to-variable magnitudes saturate here; an empty minimum (all other
+// neighbours of a check cut) takes this value.
+constexpr float kLlrCap = 1e30f;
+// Marks an unused check slot (row shorter than the kernel's maximum degree).
+constexpr uint16_t kNoEdge = 0xFFFF;
+// Limits of the compiled kernel variants.
+constexpr int kMaxRowWeight = 16;
+constexpr int kMaxColWeight = 8;
+constexpr int kMaxDRowWeight = 64;
+
+// Device-resident decoding problem, laid out for a group of G threads per
+// shot.  Variable j sits at lane j % G, pass j / G; check i at lane i % G,
+// pass i / G.  Each variable owns `cv` consecutive message slots per pass:
+// slot(p, m, u) = (p * cv + m) * G + u holds the message of its m-th edge
+// (edges of a variable in ascending check order); unused slots hold 0.
+struct DevGraph {
+    int32_t M, N, K, Md;
+    int32_t MW, NW, KW;          // words per shot of syndrome / correction / logicals
+    int32_t G;                   // threads per shot
+    int32_t pc, pv;              // check passes, variable passes
+    int32_t dc, cv;              // max row weight of H, slots per variable per pass
+    int32_t slots;               // pv * cv * G message slots per shot
+    int32_t cmw;                 // words of the per-shot variable bit mask (>= NW)
+    int32_t region;              // shared-memory words per group
+    int32_t max_iter;
+    float alpha;
+    float tie_rel;
+    uint64_t tie_seed;
+    int32_t dc_enable, dc_prior;
+    int32_t zero_ok;             // every prior < 1/2: zero syndrome decodes to zero at t = 0
+    int32_t kernel_id;
+    const uint16_t *chk_idx;     // [pc][dc][G] message slot of the check's k-th edge, or kNoEdge
+    const uint8_t *var_deg;      // [pv][G] degree of the variable (0 past N)
+    const float *lam;            // [pv][G] prior LLR ln((1-p)/p)
+    const int32_t *d_ptr;        // [Md+1] rows of D
+    const uint32_t *d_ent;       // [nnz(D)] slot of the variable's first edge | column << 16
+    const uint32_t *l_bits;      // [K][NW] rows of L as bit masks
+    const int32_t *h_ptr;        // [M+1] rows of H (sampler)
+    const int32_t *h_col;        // [E]
+    const uint32_t *thr;         // [N] floor(p * 2^32) (sampler)
+    int32_t *err_flag;           // latched device error code
+};
+
+// One batch of a decode launch (kept in device memory).
+struct BatchDesc {
+    DevGraph g;
+    int64_t B;
+    int64_t first;               // prefix of shots of earlier batches in this launch
+    const uint32_t *syn;
+    uint64_t shot_offset;
+    uint32_t *corr;
+    uint8_t *status;
+    uint32_t *lflips;
+    const uint32_t *obs_true;
+    uint32_t *iters;
+    float *post;
+    unsigned long long *counters;
+    const uint32_t *cut_in;
+};
+
+struct LaunchDesc {
+    const BatchDesc *batches;    // device array
+    int32_t n_batches;
+    int64_t total;               // shots over all batches
+    unsigned int *work;          // persistent work counter (nullptr: one group per shot)
+};
+
+// A compiled kernel variant and its limits.
+struct Variant {
+    int id;
+    int G;
+    int pc_max, dc_max, pv_max, cv_max;
+    int block_threads;
+};
+
+int num_variants();
+const Variant &variant(int id);
+// Occupancy query and launch of variant `id`.
+cudaError_t variant_attributes(int id, int smem_bytes, int *blocks_per_sm, int *regs);
+cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_bytes, cudaStream_t s);
+
+cudaError_t launch_cut_select(const DevGraph &g, int64_t B, const float *post, uint64_t shot_offset,
+                              uint32_t *cut_out, cudaStream_t s);
+cudaError_t launch_sample(const DevGraph &g, int64_t B, uint64_t seed, uint64_t shot_offset,
+                          uint32_t *syn, uint32_t *obs, uint32_t *err, cudaStream_t s);
+
+}  // namespace bpdc

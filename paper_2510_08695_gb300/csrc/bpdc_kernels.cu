@@ -1,0 +1,681 @@
+// BP+DC decoding kernels for sm_103a (arXiv 2510.08695, Sec. II.C.1 and
+// Algorithms 1-2).
+//
+// Mapping: a group of G threads decodes one shot at a time.  The shot's
+// message state lives in shared memory as one FP32 slot per Tanner-graph
+// edge, arranged variable-major (slot(p, m, u) = (p*cv + m)*G + u for the
+// m-th edge of the variable at lane u, pass p), so the variable update reads
+// and writes consecutive words across lanes.  The check update gathers the
+// slots of its row through per-lane slot indices kept in registers and
+// scatters its answers back into the same slots: every slot alternates
+// between the variable->check message q (after the variable update) and the
+// check->variable message r (after the check update).
+//
+// Flooding iteration t (t = 1 .. T_iter + 1):
+//   check phase   for every check: gather q of its row, test the row parity of
+//                 the current hard decision (carried in the least significant
+//                 mantissa bit of each q, see below), form sign / min1 / min2
+//                 and, if t <= T_iter, scatter r = alpha * sign * min(others).
+//   reduce        group-wide OR of the row-parity mismatches (a barrier that
+//                 also publishes the scatter).  None left: the hard decision
+//                 of iteration t-1 reproduces the syndrome -> converged after
+//                 t-1 iterations.  t = T_iter + 1: failed.
+//   variable      posterior L = lambda + sum r, hard decision e = [L <= 0]
+//   phase         (Eq. 4), extrinsic q = lambda + sum of the other r, tagged
+//                 with e; at t = T_iter slot 0 keeps the tagged L instead of q
+//                 so that the cut selection can read it.
+//
+// Tag: the variable update stores e_j in the least significant mantissa bit
+// of every q it writes (a change of at most one unit in the last place,
+// 2^-23 relative), so the check phase obtains the parity of the hard
+// decision over its row by XOR-ing the words it already loads.  Cut
+// variables send q = +inf (tag 0, e = 0): they never win a minimum, add no
+// sign and no parity, which is the column deletion of Algorithm 1 and the
+// zero prior of Algorithm 2.  Denormals must not be flushed (no -ftz).
+//
+// Degeneracy cutting (Algorithm 1 lines 4-7): on failure every row of D
+// gathers the tagged L^T of its support from slot 0, takes the windowed
+// maximum, breaks ties with the SplitMix64 hash of (shot, row) and sets the
+// winner's bit in a shared cut mask; BP runs again with cut variables pinned
+// to +inf and the priors of Sec. III.B.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bpdc_internal.h"
+
+namespace bpdc {
+namespace {
+
+__device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
+
+__device__ __forceinline__ float tag(float q, uint32_t e)
+{
+    return __uint_as_float((__float_as_uint(q) & ~1u) | e);
+}
+
+// SplitMix64 output number ctr of the stream keyed by key (Steele, Lea &
+// Flood 2014).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t key, uint64_t ctr)
+{
+    uint64_t z = key + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Synchronisation of the G threads that share a shot.
+template <int G>
+struct Group {
+    int u;          // lane within the group
+    int bar;        // named barrier id (G > 32)
+    unsigned mask;  // lanes of the warp that belong to the group (G <= 32)
+    int leader;     // warp lane of the group's lane 0 (G <= 32)
+
+    __device__ __forceinline__ void sync() const
+    {
+        if constexpr (G <= 32) {
+            __syncwarp(mask);
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G) : "memory");
+        }
+    }
+    // Barrier that also returns whether any lane passed a true predicate.
+    __device__ __forceinline__ bool any(bool p) const
+    {
+        if constexpr (G <= 32) {
+            __syncwarp(mask);
+            return __any_sync(mask, p) != 0;
+        } else {
+            uint32_t r;
+            asm volatile(
+                "{\n\t.reg .pred pi, po;\n\t"
+                "setp.ne.u32 pi, %1, 0;\n\t"
+                "bar.red.or.pred po, %2, %3, pi;\n\t"
+                "selp.u32 %0, 1, 0, po;\n\t}"
+                : "=r"(r)
+                : "r"((uint32_t)p), "r"(bar), "n"(G)
+                : "memory");
+            return r != 0;
+        }
+    }
+};
+
+// The cut of Algorithm 1 lines 4-7 for one shot: every row of D picks the
+// support variable of largest posterior LLR (windowed, hashed tie-break) and
+// sets its bit in cm (cm must be zero on entry).  load(slot0, col) returns
+// the posterior of a D entry.
+template <typename LoadL>
+__device__ __forceinline__ void cut_rows(const DevGraph &g, uint64_t gshot, int u, int G,
+                                         uint32_t *cm, LoadL load)
+{
+    for (int r = u; r < g.Md; r += G) {
+        const int b0 = __ldg(g.d_ptr + r), b1 = __ldg(g.d_ptr + r + 1);
+        if (b0 == b1) continue;
+        float lmax = -f_inf();
+        for (int a = b0; a < b1; ++a) {
+            const uint32_t e = __ldg(g.d_ent + a);
+            lmax = fmaxf(lmax, load(e & 0xFFFFu, e >> 16));
+        }
+        const float thr = isfinite(lmax) ? lmax - g.tie_rel * fmaxf(1.0f, fabsf(lmax)) : lmax;
+        int nc = 0;
+        for (int a = b0; a < b1; ++a) {
+            const uint32_t e = __ldg(g.d_ent + a);
+            nc += load(e & 0xFFFFu, e >> 16) >= thr;
+        }
+        if (nc == 0) continue;   // only with NaN posteriors
+        const uint64_t h = splitmix64(g.tie_seed, gshot * (uint64_t)g.Md + (uint64_t)r);
+        int pick = (int)(h % (uint64_t)nc);
+        uint32_t col = 0;
+        for (int a = b0; a < b1; ++a) {
+            const uint32_t e = __ldg(g.d_ent + a);
+            if (load(e & 0xFFFFu, e >> 16) >= thr) {
+                if (pick == 0) { col = e >> 16; break; }
+                --pick;
+            }
+        }
+        atomicOr(cm + (col >> 5), 1u << (col & 31));
+    }
+}
+
+template <int G, int PCM, int DCM, int PVM, int CVM>
+struct Lane {
+    static constexpr int kIdxWords = (PCM * DCM + 1) / 2;
+    static constexpr int kVmWords = (PVM * CVM + 31) / 32;
+
+    uint32_t idxw[kIdxWords];  // check slot indices, two u16 per word
+    uint32_t vm[kVmWords];     // bit (p*CVM + m): variable at pass p has an m-th edge
+    uint32_t vvalid;           // bit p: a variable sits at pass p
+    float lamv[PVM];           // prior LLR per variable pass
+
+    __device__ __forceinline__ uint32_t idx(int p, int k) const
+    {
+        const int n = p * DCM + k;
+        return (idxw[n >> 1] >> ((n & 1) * 16)) & 0xFFFFu;
+    }
+    __device__ __forceinline__ bool has(int p, int m) const
+    {
+        const int n = p * CVM + m;
+        return (vm[n >> 5] >> (n & 31)) & 1u;
+    }
+
+    __device__ void reload_lam(const DevGraph &g, int u)
+    {
+#pragma unroll
+        for (int p = 0; p < PVM; ++p) {
+            const int j = p * G + u;
+            lamv[p] = (p < g.pv && j < g.N) ? __ldg(g.lam + (size_t)p * G + u) : 0.0f;
+        }
+    }
+
+    __device__ void load(const DevGraph &g, int u)
+    {
+#pragma unroll
+        for (int w = 0; w < kIdxWords; ++w) idxw[w] = 0xFFFFFFFFu;
+#pragma unroll
+        for (int p = 0; p < PCM; ++p) {
+#pragma unroll
+            for (int k = 0; k < DCM; ++k) {
+                uint32_t v = kNoEdge;
+                if (p < g.pc && k < g.dc) v = __ldg(g.chk_idx + ((size_t)p * g.dc + k) * G + u);
+                const int n = p * DCM + k;
+                idxw[n >> 1] = (idxw[n >> 1] & ~(0xFFFFu << ((n & 1) * 16))) | (v << ((n & 1) * 16));
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < kVmWords; ++w) vm[w] = 0;
+        vvalid = 0;
+#pragma unroll
+        for (int p = 0; p < PVM; ++p) {
+            int deg = 0;
+            float lam = 0.0f;
+            if (p < g.pv) {
+                const int j = p * G + u;
+                if (j < g.N) {
+                    deg = __ldg(g.var_deg + (size_t)p * G + u);
+                    lam = __ldg(g.lam + (size_t)p * G + u);
+                    vvalid |= 1u << p;
+                }
+            }
+            lamv[p] = lam;
+#pragma unroll
+            for (int m = 0; m < CVM; ++m) {
+                const int n = p * CVM + m;
+                if (m < deg) vm[n >> 5] |= 1u << (n & 31);
+            }
+        }
+    }
+};
+
+template <int G, int PCM, int DCM, int PVM, int CVM>
+struct Decoder {
+    using L = Lane<G, PCM, DCM, PVM, CVM>;
+
+    // Writes the initial messages of a BP run: every variable announces its
+    // prior (tagged with its hard decision); cut variables announce +inf.
+    // Returns the hard-decision bits per pass.
+    static __device__ __forceinline__ uint32_t init(const DevGraph &g, const L &ln, const float *lam, uint32_t cut,
+                                    float *slot, int u, float *post_row)
+    {
+        uint32_t hd = 0;
+#pragma unroll
+        for (int p = 0; p < PVM; ++p) {
+            if (p < g.pv && ((ln.vvalid >> p) & 1u)) {
+                const uint32_t c = (cut >> p) & 1u;
+                const uint32_t e = (!c && lam[p] <= 0.0f) ? 1u : 0u;
+                hd |= e << p;
+                const float v = c ? f_inf() : tag(lam[p], e);
+                const int base = p * g.cv * G + u;
+#pragma unroll
+                for (int m = 0; m < CVM; ++m)
+                    if (m < g.cv && (m == 0 || ln.has(p, m))) slot[base + m * G] = v;
+                if (post_row) post_row[p * G + u] = c ? f_inf() : lam[p];
+            }
+        }
+        return hd;
+    }
+
+    // One BP run (flooding, normalized min-sum).  The slots must hold the
+    // initial messages and be visible to the whole group.  Returns whether the
+    // hard decision reproduced the syndrome; iters = iterations used; hd =
+    // hard-decision bits per variable pass.
+    static __device__ __forceinline__ bool run(const DevGraph &g, const L &ln, const Group<G> &grp, const float *lam,
+                               uint32_t cut, uint32_t sbits, float *slot, uint32_t &hd, int &iters,
+                               float *post_row)
+    {
+        const int u = grp.u;
+        const int T = g.max_iter;
+        const float alpha = g.alpha;
+        for (int t = 1;; ++t) {
+            const bool scatter = t <= T;
+            uint32_t unsat = 0;
+            // ---- check phase ----
+#pragma unroll
+            for (int p = 0; p < PCM; ++p) {
+                if (p < g.pc) {
+                    float mn1 = f_inf(), mn2 = f_inf();
+                    int kmin = 0;
+                    uint32_t negs = 0, par = 0;
+#pragma unroll
+                    for (int k = 0; k < DCM; ++k) {
+                        const uint32_t a = ln.idx(p, k);
+                        const float v = (a != kNoEdge) ? slot[a] : f_inf();
+                        const uint32_t bits = __float_as_uint(v);
+                        par ^= bits;
+                        negs |= (bits >> 31) << k;
+                        const float av = fabsf(v);
+                        const bool lt = av < mn1;
+                        mn2 = lt ? mn1 : fminf(mn2, av);
+                        mn1 = lt ? av : mn1;
+                        kmin = lt ? k : kmin;
+                    }
+                    const uint32_t s = (sbits >> p) & 1u;
+                    unsat |= (par & 1u) ^ s;
+                    if (scatter) {
+                        const uint32_t sg = s ^ (__popc(negs) & 1u);
+                        const float m1 = alpha * fminf(mn1, kLlrCap);
+                        const float m2 = alpha * fminf(mn2, kLlrCap);
+#pragma unroll
+                        for (int k = 0; k < DCM; ++k) {
+                            const uint32_t a = ln.idx(p, k);
+                            if (a != kNoEdge) {
+                                const float mag = (k == kmin) ? m2 : m1;
+                                const uint32_t neg = sg ^ ((negs >> k) & 1u);
+                                slot[a] = __uint_as_float(__float_as_uint(mag) | (neg << 31));
+                            }
+                        }
+                    }
+                }
+            }
+            if (!grp.any(unsat != 0)) { iters = t - 1; return true; }
+            if (t > T) { iters = T; return false; }
+            // ---- variable phase ----
+            const bool last = t == T;
+            uint32_t nhd = 0;
+#pragma unroll
+            for (int p = 0; p < PVM; ++p) {
+                if (p < g.pv && ((ln.vvalid >> p) & 1u)) {
+                    const int base = p * g.cv * G + u;
+                    float r[CVM];
+#pragma unroll
+                    for (int m = 0; m < CVM; ++m)
+                        r[m] = (m < g.cv && ln.has(p, m)) ? slot[base + m * G] : 0.0f;
+                    float Lp = lam[p];
+#pragma unroll
+                    for (int m = 0; m < CVM; ++m) Lp += r[m];
+                    const uint32_t c = (cut >> p) & 1u;
+                    const uint32_t e = (!c && Lp <= 0.0f) ? 1u : 0u;
+                    nhd |= e << p;
+#pragma unroll
+                    for (int m = 0; m < CVM; ++m) {
+                        if (m < g.cv && (ln.has(p, m) || (last && m == 0))) {
+                            float q = lam[p];
+#pragma unroll
+                            for (int m2 = 0; m2 < CVM; ++m2)
+                                if (m2 != m) q += r[m2];
+                            if (last && m == 0) q = Lp;
+                            slot[base + m * G] = c ? f_inf() : tag(q, e);
+                        }
+                    }
+                    if (post_row) post_row[p * G + u] = c ? f_inf() : Lp;
+                }
+            }
+            hd = nhd;
+            grp.sync();
+        }
+    }
+
+    static __device__ void decode(const LaunchDesc &ld, uint32_t *region, const Group<G> &grp, int gib)
+    {
+        (void)gib;
+        const int u = grp.u;
+        L ln;
+        const DevGraph *cur = nullptr;
+        int bi = -1;
+        int64_t bfirst = 0, bend = 0;
+        unsigned long long c_shots = 0, c_fail = 0, c_iters = 0, c_dc = 0;
+        unsigned long long *c_ptr = nullptr;
+        uint32_t bufsel = 0;
+        const int64_t groups_per_block = blockDim.x / G;
+        bool once = false;
+        bool lam_dirty = false;
+
+        while (true) {
+            // ---- next shot ----
+            int64_t w;
+            if (ld.work) {
+                unsigned long long x = 0;
+                if constexpr (G <= 32) {
+                    if (u == 0) x = atomicAdd((unsigned long long *)ld.work, 1ull);
+                    x = __shfl_sync(grp.mask, x, grp.leader);
+                } else {
+                    uint32_t *misc = region + 0;  // two words, double buffered
+                    if (u == 0) misc[bufsel] = (uint32_t)atomicAdd((unsigned long long *)ld.work, 1ull);
+                    grp.sync();
+                    x = misc[bufsel];
+                    bufsel ^= 1u;
+                }
+                w = (int64_t)x;
+            } else {
+                if (once) break;
+                once = true;
+                w = (int64_t)blockIdx.x * groups_per_block + gib;
+            }
+            if (w >= ld.total) break;
+            if (w < bfirst || w >= bend) {
+                if (c_ptr && u == 0) {
+                    atomicAdd(c_ptr + 0, c_shots);
+                    atomicAdd(c_ptr + 1, c_fail);
+                    atomicAdd(c_ptr + 2, c_iters);
+                    atomicAdd(c_ptr + 3, c_dc);
+                }
+                c_shots = c_fail = c_iters = c_dc = 0;
+                int lo = 0, hi = ld.n_batches - 1;
+                while (lo < hi) {  // last batch with first <= w
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (ld.batches[mid].first <= w) lo = mid; else hi = mid - 1;
+                }
+                bi = lo;
+                bfirst = ld.batches[bi].first;
+                bend = bfirst + ld.batches[bi].B;
+                c_ptr = ld.batches[bi].counters;
+                const DevGraph *gnew = &ld.batches[bi].g;
+                if (cur == nullptr || gnew->chk_idx != cur->chk_idx) ln.load(*gnew, u);
+                cur = gnew;
+            }
+            const BatchDesc &bd = ld.batches[bi];
+            const DevGraph g = bd.g;
+            const int64_t b = w - bfirst;
+            const uint64_t gshot = bd.shot_offset + (uint64_t)b;
+            float *slot = reinterpret_cast<float *>(region + 2);
+            uint32_t *cm = region + 2 + g.slots;     // cut mask, then e_hat staging
+            uint32_t *ls = cm + g.cmw;               // logical-flip staging
+            float *post_row = bd.post ? bd.post + (size_t)b * g.N : nullptr;
+            const uint32_t *cut_in = bd.cut_in;
+
+            // ---- a1: syndrome bits of my checks ----
+            uint32_t sbits = 0;
+            const uint32_t *sy = bd.syn + (size_t)b * g.MW;
+#pragma unroll
+            for (int p = 0; p < PCM; ++p) {
+                const int i = p * G + u;
+                if (p < g.pc && i < g.M) sbits |= ((__ldg(sy + (i >> 5)) >> (i & 31)) & 1u) << p;
+            }
+            const bool nonzero = grp.any(sbits != 0);
+
+            uint32_t hd = 0, cut = 0;
+            int st = 0, it1 = 0, it2 = 0;
+            bool ran_dc = false;
+            if (lam_dirty) { ln.reload_lam(g, u); lam_dirty = false; }
+            if (cut_in) {
+                // BP on a given cut graph (Algorithm 2 form), no DC
+                const uint32_t *ci = cut_in + (size_t)b * g.NW;
+#pragma unroll
+                for (int p = 0; p < PVM; ++p) {
+                    const int j = p * G + u;
+                    if (p < g.pv && j < g.N) cut |= ((__ldg(ci + (j >> 5)) >> (j & 31)) & 1u) << p;
+                }
+            }
+            if (!cut_in && !nonzero && g.zero_ok) {
+                // converged before the first iteration: e_hat = 0
+                if (post_row) {
+#pragma unroll
+                    for (int p = 0; p < PVM; ++p)
+                        if (p < g.pv && ((ln.vvalid >> p) & 1u)) post_row[p * G + u] = ln.lamv[p];
+                }
+            } else {
+                for (bool second = false;; second = true) {
+                    hd = init(g, ln, ln.lamv, cut, slot, u, post_row);
+                    grp.sync();
+                    int iters = 0;
+                    const bool ok = run(g, ln, grp, ln.lamv, cut, sbits, slot, hd, iters, post_row);
+                    if (second) it2 = iters; else it1 = iters;
+                    if (ok) { st = second ? 1 : 0; break; }
+                    if (second || cut_in || !g.dc_enable) { st = 2; break; }
+                    // ---- a7: cut selection on the last posterior (slot 0) ----
+                    ran_dc = true;
+                    for (int x = u; x < g.cmw; x += G) cm[x] = 0;
+                    grp.sync();
+                    cut_rows(g, gshot, u, G, cm, [&](uint32_t s0, uint32_t) { return slot[s0]; });
+                    grp.sync();
+#pragma unroll
+                    for (int p = 0; p < PVM; ++p) {
+                        const int j = p * G + u;
+                        if (p < g.pv && ((ln.vvalid >> p) & 1u)) {
+                            cut |= ((cm[j >> 5] >> (j & 31)) & 1u) << p;
+                            if (g.dc_prior) {
+                                // first-run posterior as prior, p_hat clamped to [1e-12, 1/2]
+                                const float Lj =
+                                    __uint_as_float(__float_as_uint(slot[p * g.cv * G + u]) & ~1u);
+                                ln.lamv[p] = fminf(fmaxf(Lj, 0.0f), 27.631021115928547f);
+                                lam_dirty = true;
+                            }
+                        }
+                    }
+                    grp.sync();
+                    // ---- a8: BP again on the cut graph ----
+                }
+            }
+
+            // ---- a9: epilogue ----
+            uint32_t *corr = bd.corr + (size_t)b * g.NW;
+            bool fail_local = false;
+            const bool any_set = grp.any(hd != 0);
+            if (!any_set) {
+                for (int x = u; x < g.NW; x += G) corr[x] = 0;
+                for (int x = u; x < g.KW; x += G) {
+                    if (bd.lflips) bd.lflips[(size_t)b * g.KW + x] = 0;
+                    if (bd.obs_true && __ldg(bd.obs_true + (size_t)b * g.KW + x) != 0) fail_local = true;
+                }
+            } else {
+                for (int x = u; x < g.NW; x += G) cm[x] = 0;
+                for (int x = u; x < g.KW; x += G) ls[x] = 0;
+                grp.sync();
+#pragma unroll
+                for (int p = 0; p < PVM; ++p) {
+                    if ((hd >> p) & 1u) {
+                        const int j = p * G + u;
+                        atomicOr(cm + (j >> 5), 1u << (j & 31));
+                        const uint32_t *lc = g.l_bits + (size_t)j * g.KW;
+                        for (int x = 0; x < g.KW; ++x) {
+                            const uint32_t v = __ldg(lc + x);
+                            if (v) atomicXor(ls + x, v);
+                        }
+                    }
+                }
+                grp.sync();
+                for (int x = u; x < g.NW; x += G) corr[x] = cm[x];
+                for (int x = u; x < g.KW; x += G) {
+                    const uint32_t v = ls[x];
+                    if (bd.lflips) bd.lflips[(size_t)b * g.KW + x] = v;
+                    if (bd.obs_true && __ldg(bd.obs_true + (size_t)b * g.KW + x) != v) fail_local = true;
+                }
+            }
+            const bool fail = grp.any(fail_local) || st == 2;
+            if (u == 0) {
+                bd.status[b] = (uint8_t)st;
+                if (bd.iters) bd.iters[b] = (uint32_t)it1 | ((uint32_t)it2 << 16);
+            }
+            c_shots += 1;
+            c_fail += fail ? 1 : 0;
+            c_iters += (unsigned long long)(it1 + it2);
+            c_dc += ran_dc ? 1 : 0;
+        }
+        if (c_ptr && u == 0) {
+            atomicAdd(c_ptr + 0, c_shots);
+            atomicAdd(c_ptr + 1, c_fail);
+            atomicAdd(c_ptr + 2, c_iters);
+            atomicAdd(c_ptr + 3, c_dc);
+        }
+    }
+};
+
+template <int G, int PCM, int DCM, int PVM, int CVM, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int region_words)
+{
+    extern __shared__ uint32_t smem[];
+    const int tid = threadIdx.x;
+    const int gib = tid / G;
+    Group<G> grp;
+    grp.u = tid % G;
+    grp.bar = 1 + gib;
+    if constexpr (G <= 32) {
+        const int wl = tid & 31;
+        const int base = (wl / G) * G;
+        grp.mask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << base);
+        grp.leader = base;
+    } else {
+        grp.mask = 0xFFFFFFFFu;
+        grp.leader = 0;
+    }
+    uint32_t *region = smem + (size_t)gib * region_words;
+    Decoder<G, PCM, DCM, PVM, CVM>::decode(ld, region, grp, gib);
+}
+
+// Cut selection alone, one block per shot (same selection code as the fused kernel).
+__global__ void cut_select_kernel(DevGraph g, int64_t B, const float *post, uint64_t shot_offset,
+                                  uint32_t *cut_out)
+{
+    extern __shared__ uint32_t sm[];
+    uint32_t *cm = sm;
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        for (int x = threadIdx.x; x < g.NW; x += blockDim.x) cm[x] = 0;
+        __syncthreads();
+        const float *row = post + (size_t)b * g.N;
+        cut_rows(g, shot_offset + (uint64_t)b, threadIdx.x, blockDim.x, cm,
+                 [&](uint32_t, uint32_t col) { return __ldg(row + col); });
+        __syncthreads();
+        for (int x = threadIdx.x; x < g.NW; x += blockDim.x) cut_out[(size_t)b * g.NW + x] = cm[x];
+        __syncthreads();
+    }
+}
+
+// Seeded sampler: errors, syndromes e H^T and observables e L^T, one block per shot.
+__global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t shot_offset,
+                              uint32_t *syn, uint32_t *obs, uint32_t *err)
+{
+    extern __shared__ uint32_t sm[];
+    uint32_t *eb = sm, *sb = sm + g.NW, *ob = sb + g.MW;
+    const int nw = g.NW + g.MW + g.KW;
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        for (int x = threadIdx.x; x < nw; x += blockDim.x) sm[x] = 0;
+        __syncthreads();
+        const uint64_t gs = shot_offset + (uint64_t)b;
+        for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
+            const uint64_t h = splitmix64(seed, gs * (uint64_t)g.N + (uint64_t)j);
+            if ((uint32_t)(h >> 32) < __ldg(g.thr + j)) atomicOr(eb + (j >> 5), 1u << (j & 31));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < g.M; i += blockDim.x) {
+            uint32_t par = 0;
+            for (int a = __ldg(g.h_ptr + i); a < __ldg(g.h_ptr + i + 1); ++a) {
+                const int c = __ldg(g.h_col + a);
+                par ^= (eb[c >> 5] >> (c & 31)) & 1u;
+            }
+            if (par) atomicOr(sb + (i >> 5), 1u << (i & 31));
+        }
+        for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
+            if ((eb[j >> 5] >> (j & 31)) & 1u) {
+                for (int x = 0; x < g.KW; ++x) {
+                    const uint32_t v = __ldg(g.l_bits + (size_t)j * g.KW + x);
+                    if (v) atomicXor(ob + x, v);
+                }
+            }
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < g.MW; x += blockDim.x) syn[(size_t)b * g.MW + x] = sb[x];
+        if (obs)
+            for (int x = threadIdx.x; x < g.KW; x += blockDim.x) obs[(size_t)b * g.KW + x] = ob[x];
+        if (err)
+            for (int x = threadIdx.x; x < g.NW; x += blockDim.x) err[(size_t)b * g.NW + x] = eb[x];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Variant table: (id, G, checks passes, row weight, variable passes, slots per
+// variable, block threads).
+#define BPDC_VARIANTS(X)                \
+    X(0, 8, 9, 6, 18, 3, 256, 3)        \
+    X(1, 16, 5, 6, 9, 3, 256, 3)        \
+    X(2, 32, 3, 6, 5, 3, 256, 3)        \
+    X(3, 4, 9, 6, 18, 3, 256, 3)        \
+    X(4, 256, 5, 8, 11, 4, 256, 3)      \
+    X(5, 512, 3, 8, 6, 4, 512, 2)       \
+    X(6, 128, 10, 8, 22, 4, 128, 6)     \
+    X(7, 8, 9, 8, 18, 4, 256, 3)
+
+static const Variant kVariants[] = {
+#define X(id, G, PC, DC, PV, CV, BLK, MB) {id, G, PC, DC, PV, CV, BLK},
+    BPDC_VARIANTS(X)
+#undef X
+};
+
+int num_variants() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
+const Variant &variant(int id) { return kVariants[id]; }
+
+static const void *variant_fn(int id)
+{
+    switch (id) {
+#define X(id, G, PC, DC, PV, CV, BLK, MB) \
+    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, BLK, MB>;
+        BPDC_VARIANTS(X)
+#undef X
+    default: return nullptr;
+    }
+}
+
+cudaError_t variant_attributes(int id, int smem_bytes, int *blocks_per_sm, int *regs)
+{
+    const void *fn = variant_fn(id);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (regs) *regs = fa.numRegs;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kVariants[id].block_threads,
+                                                         smem_bytes);
+}
+
+cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_bytes, cudaStream_t s)
+{
+    const int region = smem_bytes / 4 / (kVariants[id].block_threads / kVariants[id].G);
+    switch (id) {
+#define X(id, G, PC, DC, PV, CV, BLK, MB)                                                     \
+    case id:                                                                                  \
+        decode_kernel<G, PC, DC, PV, CV, BLK, MB><<<grid, BLK, smem_bytes, s>>>(ld, region); \
+        return cudaGetLastError();
+        BPDC_VARIANTS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_cut_select(const DevGraph &g, int64_t B, const float *post, uint64_t shot_offset,
+                              uint32_t *cut_out, cudaStream_t s)
+{
+    if (B <= 0) return cudaSuccess;
+    const int grid = (int)(B < 65536 ? B : 65536);
+    cut_select_kernel<<<grid, 256, g.NW * 4, s>>>(g, B, post, shot_offset, cut_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const DevGraph &g, int64_t B, uint64_t seed, uint64_t shot_offset,
+                          uint32_t *syn, uint32_t *obs, uint32_t *err, cudaStream_t s)
+{
+    if (B <= 0) return cudaSuccess;
+    const int smem = (g.NW + g.MW + g.KW) * 4;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute((const void *)sample_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = (int)(B < 152 * 16 ? B : 152 * 16);
+    sample_kernel<<<grid, 256, smem, s>>>(g, B, seed, shot_offset, syn, obs, err);
+    return cudaGetLastError();
+}
+
+}  // namespace bpdc

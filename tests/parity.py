@@ -1,0 +1,86 @@
+"""Helpers that compare the CUDA decoder with the FP64 oracle shot by shot.
+
+Acceptance (FP32 GPU vs FP64 oracle):
+  * a shot is *comparable* when the oracle's final posterior has |L_j| >= 1e-3
+    for every variable and, if the shot ran degeneracy cutting, its first-run
+    posterior also has |L_j| >= 1e-3 and every row of D is *robust*: no
+    support variable lies within 1e-6 * max(1, |L_max|) of the tie-window
+    edge L_max - tie_rel * max(1, |L_max|) (so FP32 rounding cannot change the
+    candidate set);
+  * on comparable shots status, corrections, logical flips and iteration
+    counts are bit-exact;
+  * over all shots the failure counts agree within 2 binomial sigma.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from bpdc_inputs.sampler import pack_bits, unpack_bits
+
+LLR_EPS = 1e-3
+WINDOW_EPS = 1e-6
+
+
+def to_dev(bits_u8: np.ndarray):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(pack_bits(bits_u8)).view(np.int32)).cuda()
+
+
+def from_dev(words, n: int) -> np.ndarray:
+    return unpack_bits(words.cpu().numpy().view(np.uint32), n)
+
+
+def robust_rows(D, post1: np.ndarray, tie_rel: float) -> np.ndarray:
+    """bool [B]: every row of D has its candidate set decided away from the window edge."""
+    D = D.tocsr()
+    ok = np.ones(post1.shape[0], dtype=bool)
+    for r in range(D.shape[0]):
+        sup = D.indices[D.indptr[r]:D.indptr[r + 1]]
+        if sup.size == 0:
+            continue
+        v = post1[:, sup]
+        lmax = v.max(1)
+        scale = np.maximum(1.0, np.abs(lmax))
+        thr = lmax - tie_rel * scale
+        near = (np.abs(v - thr[:, None]) <= WINDOW_EPS * scale[:, None]) & (v != lmax[:, None])
+        ok &= ~near.any(1)
+    return ok
+
+
+def comparable(problem, ref: dict, tie_rel: float) -> np.ndarray:
+    post = ref["post"]
+    finite = np.where(np.isinf(post), np.inf, np.abs(post))
+    ok = finite.min(1) >= LLR_EPS
+    dc = ref["status"] > 0
+    if dc.any():
+        p1 = ref["post1"][dc]
+        ok_dc = (np.abs(p1).min(1) >= LLR_EPS) & robust_rows(problem.D, p1, tie_rel)
+        ok[dc] &= ok_dc
+    return ok
+
+
+def compare(problem, gpu_out: dict, ref: dict, obs: np.ndarray | None, tie_rel: float) -> dict:
+    """Returns counts and the indices of comparable shots that differ."""
+    N, K = problem.N, problem.K
+    st = gpu_out["status"].cpu().numpy()
+    e = from_dev(gpu_out["corrections"], N)
+    f = from_dev(gpu_out["logical_flips"], K) if K else np.zeros((len(st), 0), np.uint8)
+    it = gpu_out["iterations"].cpu().numpy().view(np.uint32)
+    it1, it2 = it & 0xFFFF, it >> 16
+    comp = comparable(problem, ref, tie_rel)
+    same = ((st == ref["status"]) & (e == ref["e_hat"]).all(1) & (f == ref["obs_pred"]).all(1)
+            & (it1 == ref["iters1"]) & (it2 == ref["iters2"]))
+    rep = dict(B=len(st), comparable=int(comp.sum()), mismatched=np.nonzero(comp & ~same)[0],
+               identical_all=int(same.sum()), status_gpu=np.bincount(st, minlength=3),
+               status_ref=np.bincount(ref["status"], minlength=3))
+    if obs is not None:
+        fail_g = (st == 2) | (f != obs).any(1)
+        fail_o = (ref["status"] == 2) | (ref["obs_pred"] != obs).any(1)
+        rep["fail_gpu"], rep["fail_ref"] = int(fail_g.sum()), int(fail_o.sum())
+    return rep
+
+
+def within_2_sigma(k1: int, k2: int, n: int) -> bool:
+    p = max((k1 + k2) / (2.0 * n), 1.0 / n)
+    sigma = np.sqrt(n * p * (1 - p))
+    return abs(k1 - k2) <= 2 * sigma + 1

@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA decoder, called through the C-ABI, against the FP64
+oracle on the same seeded shots (acceptance rules in tests/parity.py)."""
+import numpy as np
+import pytest
+
+import bpdc_inputs as bi
+from bpdc_inputs.sampler import sample_shots, syndromes, unpack_bits
+from parity import compare, comparable, from_dev, robust_rows, to_dev, within_2_sigma
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x2510086950
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def pkg(torch_cuda):
+    import paper_2510_08695_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def _run(pkg, oracle_mod, P, B, opts_kw, seed=SEED, offset=0, G=None, persistent=True):
+    _, s, o = sample_shots(P, seed, offset, B)
+    opts = pkg.Options(**opts_kw)
+    g = pkg.Graph.from_problem(P, opts)
+    if G:
+        g.set_plan(G)
+    out = g.decode(to_dev(s), offset, obs_true=to_dev(o), persistent=persistent)
+    g.sync_status()
+    ref = oracle_mod.decode_batch(P, s, offset,
+                                  oracle_mod.Options(alpha=opts.ms_scale, max_iter=opts.max_iter,
+                                                     dc_enable=opts.dc_enable, dc_prior=opts.dc_prior,
+                                                     tie_rel=opts.tie_rel, tie_seed=opts.tie_seed),
+                                  want_post=True, want_post1=True, want_cut=True)
+    return g, s, o, out, ref
+
+
+def _assert_parity(P, out, ref, o, tie_rel, min_comparable=0.9):
+    rep = compare(P, out, ref, o, tie_rel)
+    assert rep["comparable"] >= min_comparable * rep["B"], rep
+    assert len(rep["mismatched"]) == 0, (rep, rep["mismatched"][:20])
+    assert within_2_sigma(rep["fail_gpu"], rep["fail_ref"], rep["B"]), rep
+    return rep
+
+
+# ---------------------------------------------------------------------------
+# sampler
+
+@pytest.mark.parametrize("name", ["bb72", "hgp", "phen"])
+def test_gpu_sampler_bit_exact(pkg, name):
+    P = {"bb72": lambda: bi.bb_problem("bb72", 0.05), "hgp": lambda: bi.hgp_problem(0.07),
+         "phen": lambda: bi.phenomenological_bb_problem("bb72", 3, 0.02)}[name]()
+    g = pkg.Graph.from_problem(P)
+    B, off = 3000, 12345
+    syn, obs, err = g.sample(B, SEED + 7, off, errors=True)
+    e, s, o = sample_shots(P, SEED + 7, off, B)
+    assert (from_dev(err, P.N) == e).all()
+    assert (from_dev(syn, P.M) == s).all()
+    assert (from_dev(obs, P.K) == o).all()
+
+
+# ---------------------------------------------------------------------------
+# full BP+DC against the oracle
+
+def test_cfg_bb72_code_capacity_parity(pkg, oracle_mod):
+    """BB [[72,12,6]], p = 0.05, 10^4 shots, alpha = 0.625, T_iter = 50."""
+    P = bi.bb_problem("bb72", 0.05)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 10000, dict(ms_scale=0.625, max_iter=50))
+    rep = _assert_parity(P, out, ref, o, 1e-5)
+    assert rep["status_ref"][1] > 50 and rep["status_ref"][2] > 50
+
+
+@pytest.mark.parametrize("G", [4, 8, 16, 32])
+def test_bb144_parity_every_small_plan(pkg, oracle_mod, G):
+    P = bi.bb_problem("bb144", 0.06)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 3000, dict(ms_scale=0.625, max_iter=50), G=G)
+    assert g.info["threads_per_shot"] == G
+    _assert_parity(P, out, ref, o, 1e-5)
+
+
+@pytest.mark.parametrize("G", [128, 256, 512])
+def test_hgp_parity(pkg, oracle_mod, G):
+    P = bi.hgp_problem(0.06)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 600, dict(ms_scale=0.625, max_iter=50), G=G)
+    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.8)
+
+
+def test_phenomenological_parity(pkg, oracle_mod):
+    P = bi.phenomenological_bb_problem("bb144", 12, 0.006)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 300, dict(ms_scale=0.625, max_iter=200))
+    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.8)
+
+
+def test_alpha_one_and_posterior_prior_parity(pkg, oracle_mod):
+    P = bi.bb_problem("bb72", 0.06)
+    for kw in (dict(ms_scale=1.0, max_iter=72), dict(ms_scale=0.625, max_iter=40, dc_prior=1)):
+        g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, kw)
+        _assert_parity(P, out, ref, o, 1e-5)
+
+
+# ---------------------------------------------------------------------------
+# single steps
+
+def test_cut_select_matches_oracle(pkg, oracle_mod, torch_cuda):
+    torch = torch_cuda
+    P = bi.bb_problem("bb144", 0.07)
+    _, s, _ = sample_shots(P, SEED + 3, 0, 3000)
+    ref = oracle_mod.decode_batch(P, s, 0, oracle_mod.Options(max_iter=30), want_post1=True, want_cut=True)
+    idx = np.nonzero(ref["status"] > 0)[0]
+    assert idx.size > 50
+    post = ref["post1"][idx].astype(np.float32)
+    g = pkg.Graph.from_problem(P)
+    # shot offsets must match the oracle's (global index = position in the batch)
+    cuts = []
+    for k, b in enumerate(idx):
+        c = g.cut_select(torch.from_numpy(post[k][None, :]).cuda(), int(b))
+        cuts.append(from_dev(c, P.N)[0])
+    cuts = np.array(cuts)
+    ok = robust_rows(P.D, ref["post1"][idx], 1e-5)
+    assert ok.mean() > 0.8
+    assert (cuts[ok] == ref["cut"][idx][ok]).all()
+
+
+def test_bp_on_given_cut_matches_oracle(pkg, oracle_mod):
+    """BP #2 alone: the oracle's cut sets fed to the GPU (cut_in) and to the
+    oracle's BP with +inf priors on the cut (Algorithm 2)."""
+    P = bi.bb_problem("bb72", 0.06)
+    _, s, _ = sample_shots(P, SEED + 4, 0, 4000)
+    oo = oracle_mod.Options(max_iter=40)
+    ref = oracle_mod.decode_batch(P, s, 0, oo, want_cut=True)
+    idx = np.nonzero(ref["status"] > 0)[0][:300]
+    g = pkg.Graph.from_problem(P, pkg.Options(max_iter=40))
+    out = g.decode(to_dev(s[idx]), 0, cut_in=to_dev(ref["cut"][idx]))
+    st = out["status"].cpu().numpy()
+    e = from_dev(out["corrections"], P.N)
+    it = out["iterations"].cpu().numpy() & 0xFFFF
+    lam0 = oracle_mod.prior_llr(P.priors)
+    n_cmp = 0
+    for k, b in enumerate(idx):
+        lam = np.where(ref["cut"][b] > 0, np.inf, lam0)
+        ok, e_o, post, its = oracle_mod.bp(P, s[b], lam=lam, opts=oo)
+        fin = np.abs(post[np.isfinite(post)])
+        if fin.size and fin.min() < 1e-3:
+            continue
+        n_cmp += 1
+        assert st[k] == (0 if ok else 2) and (e[k] == e_o).all() and it[k] == its, b
+    assert n_cmp > 0.8 * len(idx)
+
+
+# ---------------------------------------------------------------------------
+# launch forms, splitting, edge cases
+
+def test_plain_and_persistent_identical_and_offsets(pkg):
+    P = bi.bb_problem("bb144", 0.06)
+    _, s, o = sample_shots(P, SEED + 5, 1000, 2500)
+    g = pkg.Graph.from_problem(P)
+    a = g.decode(to_dev(s), 1000, persistent=True)
+    b = g.decode(to_dev(s), 1000, persistent=False)
+    c1 = g.decode(to_dev(s[:777]), 1000)
+    c2 = g.decode(to_dev(s[777:]), 1777)
+    for k in ("corrections", "status", "logical_flips", "iterations"):
+        assert (a[k] == b[k]).all(), k
+        import torch
+        assert (a[k] == torch.cat([c1[k], c2[k]])).all(), k
+
+
+def test_decode_multi_equals_single(pkg):
+    import torch
+    probs = [bi.bb_problem("bb72", 0.04), bi.bb_problem("bb144", 0.05), bi.hgp_problem(0.05),
+             bi.bb_problem("bb72", 0.08)]
+    items, singles = [], []
+    for i, P in enumerate(probs):
+        _, s, o = sample_shots(P, SEED + 10 + i, 0, 700 if P.N > 200 else 2000)
+        g = pkg.Graph.from_problem(P)
+        syn, obs = to_dev(s), to_dev(o)
+        singles.append(g.decode(syn, 0, obs_true=obs))
+        items.append(dict(graph=g, syndromes=syn, shot_offset=0, obs_true=obs,
+                          out=g.alloc_outputs(s.shape[0]),
+                          counters=torch.zeros(4, dtype=torch.int64, device="cuda")))
+    pkg.decode_multi(items)
+    torch.cuda.synchronize()
+    for it, ref in zip(items, singles):
+        for k in ("corrections", "status", "logical_flips", "iterations"):
+            assert (it["out"][k] == ref[k]).all(), k
+        cnt = it["counters"].cpu().numpy()
+        st = ref["status"].cpu().numpy()
+        assert cnt[0] == len(st) and cnt[3] == (st > 0).sum()
+
+
+def test_edge_cases(pkg, oracle_mod, torch_cuda):
+    torch = torch_cuda
+    P = bi.bb_problem("bb72", 0.05)
+    g = pkg.Graph.from_problem(P)
+    # B = 0 is a no-op
+    out = g.decode(torch.zeros((0, g.MW), dtype=torch.int32, device="cuda"), 0)
+    assert out["status"].numel() == 0
+    # zero syndromes decode to zero at iteration 0
+    z = g.decode(torch.zeros((64, g.MW), dtype=torch.int32, device="cuda"), 0)
+    assert (z["corrections"] == 0).all() and (z["status"] == 0).all() and (z["iterations"] == 0).all()
+    # a single shot, every single-qubit error of BB72
+    E = np.eye(P.N, dtype=np.uint8)
+    s = syndromes(E, P.H)
+    one = g.decode(to_dev(s[:1]), 0)
+    assert (from_dev(one["corrections"], P.N)[0] == E[0]).all()
+    allq = g.decode(to_dev(s), 0)
+    assert (from_dev(allq["corrections"], P.N) == E).all() and (allq["status"] == 0).all()
+    # T_iter = 0: nonzero syndromes fail BP at once, DC runs on the priors
+    _, s2, _ = sample_shots(P, SEED + 6, 0, 500)
+    g0 = pkg.Graph.from_problem(P, pkg.Options(max_iter=0))
+    r0 = g0.decode(to_dev(s2), 0)
+    ref0 = oracle_mod.decode_batch(P, s2, 0, oracle_mod.Options(max_iter=0))
+    assert (r0["status"].cpu().numpy() == ref0["status"]).all()
+    # DC disabled: status is 0 or 2 only
+    gd = pkg.Graph.from_problem(P, pkg.Options(dc_enable=0))
+    rd = gd.decode(to_dev(s2), 0)
+    assert set(np.unique(rd["status"].cpu().numpy())) <= {0, 2}
+    # converged shots reproduce their syndrome
+    rs = g.decode(to_dev(s2), 0)
+    st = rs["status"].cpu().numpy()
+    e = from_dev(rs["corrections"], P.N)
+    assert (syndromes(e[st < 2], P.H) == s2[st < 2]).all()
+
+
+def test_posterior_output(pkg, oracle_mod):
+    P = bi.bb_problem("bb72", 0.05)
+    _, s, _ = sample_shots(P, SEED + 8, 0, 3000)
+    g = pkg.Graph.from_problem(P)
+    out = g.decode(to_dev(s), 0, posterior=True)
+    ref = oracle_mod.decode_batch(P, s, 0, oracle_mod.Options(), want_post=True, want_post1=True)
+    post = out["posterior_llr"].cpu().numpy().astype(np.float64)
+    comp = comparable(P, ref, 1e-5) & (ref["status"] == 0)
+    rp = ref["post"][comp]
+    gp = post[comp]
+    assert comp.sum() > 1000
+    inf = np.isinf(rp)
+    assert (np.isinf(gp) == inf).all()
+    rel = np.abs(gp[~inf] - rp[~inf]) / np.maximum(np.abs(rp[~inf]), 1.0)
+    assert rel.max() < 1e-4, rel.max()
