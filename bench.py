@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the BP+DC hot path (one JSON line on rank 0).
+
+Workload (batched code capacity across uneven codes): BB [[144,12,12]],
+BB [[72,12,6]] and the hypergraph product of a seeded (3,4)-regular n = 40
+code (n = 2500, k = 148); bit-flip rate p = 0.01 .. 0.10 (10 values);
+10^6 shots per (code, p); normalized min-sum, alpha = 0.625, T_iter = 50,
+FP32 messages, degeneracy cutting on BP failure, second BP on the priors.
+A step decodes all 3 * 10 * 10^6 shots; shots are sampled on the GPU by the
+seeded counter sampler before timing (they stay resident in HBM; at ~2 GB
+of syndromes they exceed L2, so no flush is needed).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 the script runs under torch.distributed.run, one process
+per GPU; every rank decodes its own 3 * 10^7 shots (disjoint global shot
+indices), so per-GPU work is fixed (weak scaling); the only cross-rank
+operations are a barrier and a max of the elapsed times.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "BP+DC shots/s and p99 us/shot at matched LER vs plain kernel, 1 GB300"
+UNIT = "shots/s"
+SEED = 0x2510086950 + 1          # workload seed (second workload configuration)
+P_VALUES = [round(0.01 * i, 2) for i in range(1, 11)]
+CODES = ["bb144", "bb72", "hgp2500"]
+ALPHA, T_ITER = 0.625, 50
+SMEM_BYTES_PER_CLK_PER_SM = 128   # 32 banks x 4 B
+EDGE_UPDATE_BYTES = 16            # 2 x 4 B read + 2 x 4 B written per edge and iteration
+
+
+# ---------------------------------------------------------------------------
+# host helpers (no GPU needed; covered by tests/test_bench_host.py)
+
+def shard_offset(rank: int, shots_per_point: int) -> int:
+    """First global shot index of a rank's share of every (code, p) point."""
+    return rank * shots_per_point
+
+
+def workload_problems():
+    import bpdc_inputs as bi
+    probs = []
+    for code in CODES:
+        for p in P_VALUES:
+            if code == "hgp2500":
+                probs.append((code, p, bi.hgp_problem(p)))
+            else:
+                probs.append((code, p, bi.bb_problem(code, p)))
+    return probs
+
+
+def extrapolate_cpu(samples, shots_per_point: int) -> float:
+    """CPU shots/s for the full workload from per-point (shots, seconds) samples."""
+    total_time = sum(shots_per_point * t / n for n, t in samples)
+    return len(samples) * shots_per_point / total_time
+
+
+def oracle_sample_plan(code: str) -> int:
+    return 400 if code == "hgp2500" else 4000
+
+
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        under_load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(under_load) if under_load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle timed on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from bpdc_inputs.sampler import sample_shots
+    oracle.build()
+    cores = oracle.max_threads()
+    probs = workload_problems()
+    opts = oracle.Options(alpha=ALPHA, max_iter=T_ITER)
+    inputs = []
+    for i, (code, p, P) in enumerate(probs):
+        n = max(1, oracle_sample_plan(code) // 4)
+        _, s, _ = sample_shots(P, SEED, 0, n)
+        inputs.append((P, s))
+    per_step = []
+    for step in range(args.warmup + args.steps):
+        samples = []
+        for P, s in inputs:
+            t0 = time.perf_counter()
+            oracle.decode_batch(P, s, 0, opts)
+            samples.append((s.shape[0], time.perf_counter() - t0))
+        if step >= args.warmup:
+            per_step.append(extrapolate_cpu(samples, args.shots_per_point))
+    value = statistics.median(per_step)
+    sample_desc = (f"{sum(s.shape[0] for _, s in inputs)} shots per step: first "
+                   f"{oracle_sample_plan('bb72') // 4} (BB) / {oracle_sample_plan('hgp2500') // 4} (HGP) shots of "
+                   "each (code, p) point, extrapolated per point to 1e6 shots")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded counter sampler)",
+            "config": config_dict(args, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample_desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, world):
+    return {"workload": "batched code capacity across uneven codes: BB[[144,12,12]], BB[[72,12,6]], "
+                        "HGP of a seeded (3,4)-regular n=40 code (n=2500, k=148); p=0.01..0.10 (10 values); "
+                        f"{args.shots_per_point} shots per (code,p) per GPU; normalized min-sum alpha=0.625, "
+                        "T_iter=50, DC on failure, second BP on priors p",
+            "shots_per_step": len(CODES) * len(P_VALUES) * args.shots_per_point * world,
+            "launch": "persistent multi-batch launches (one per kernel variant), device work counter",
+            "l2": "inputs larger than L2 (no flush)",
+            "parallelism": f"dp{world}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shots-per-point", type=int, default=1_000_000)
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/latency/cpu legs")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2510_08695_gb300 as pkg
+    from paper_2510_08695_gb300 import build as pbuild
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        dist.barrier()
+    pkg.load(build_if_missing=False)
+
+    spp = args.shots_per_point
+    off = shard_offset(rank, spp)
+    probs = workload_problems()
+    opts = pkg.Options(ms_scale=ALPHA, max_iter=T_ITER)
+    batches = []
+    for code, p, P in probs:
+        g = pkg.Graph.from_problem(P, opts, device=local)
+        syn, obs, _ = g.sample(spp, SEED, off)
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        batches.append(dict(code=code, p=p, P=P, graph=g, syndromes=syn, obs_true=obs, shot_offset=off,
+                            out=g.alloc_outputs(spp), counters=cnt))
+    torch.cuda.synchronize()
+    groups = {}
+    for b in batches:
+        groups.setdefault(b["graph"].info["kernel_id"], []).append(b)
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        for gi, (vid, items) in enumerate(sorted(groups.items())):
+            if events is not None:
+                events[gi][0].record(stream)
+            pkg.decode_multi(items, stream)
+            if events is not None:
+                events[gi][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for b in batches:
+        b["counters"].zero_()
+    step()     # one counted step: iterations and failures per batch
+    torch.cuda.synchronize()
+    iters = {id(b): int(b["counters"][2]) for b in batches}
+    fails = {id(b): int(b["counters"][1]) for b in batches}
+
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in groups] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    shots_per_step = len(batches) * spp * world
+    value = shots_per_step * args.steps / (ms / 1e3)
+
+    # dominant launch: per-variant average duration and algorithmic bytes
+    per_variant = []
+    for gi, (vid, items) in enumerate(sorted(groups.items())):
+        d_ms = statistics.mean(ev[k][gi][0].elapsed_time(ev[k][gi][1]) for k in range(args.steps))
+        eu = sum(iters[id(b)] * b["graph"].E for b in items)
+        per_variant.append(dict(kernel_id=vid, ms=d_ms, edge_updates=eu, codes=sorted({b["code"] for b in items})))
+    dom = max(per_variant, key=lambda v: v["ms"])
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_gbs = nsm * SMEM_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9
+    achieved_gbs = dom["edge_updates"] * EDGE_UPDATE_BYTES / (dom["ms"] / 1e3) / 1e9
+    total_eu = sum(v["edge_updates"] for v in per_variant)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded counter sampler on the GPU, bit-identical to the CPU sampler)",
+            "config": config_dict(args, world),
+            "edge_updates_per_s": total_eu * world / (ms / args.steps / 1e3),
+            "roofline": {"bound": "smem", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": achieved_gbs / peak_gbs, "traffic": None,
+                         "kernel": f"decode_kernel variant {dom['kernel_id']} ({'+'.join(dom['codes'])})",
+                         "peak_source": f"{nsm} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x median sampled SM clock "
+                                        f"{sm_mhz:.0f} MHz",
+                         "algorithmic_bytes": f"{EDGE_UPDATE_BYTES} B per edge-update x "
+                                              f"{dom['edge_updates']} edge-updates per launch"},
+            "per_variant_ms": {str(v["kernel_id"]): round(v["ms"], 3) for v in per_variant},
+            "gpu_launches": args.steps * len(groups),
+            "clocks": clk}
+
+    if rank == 0 and not args.no_extras:
+        extras(args, pkg, torch, batches, groups, stream, line, value, fails)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
+    import numpy as np
+
+    # ---- plain per-batch kernel on the same shots: throughput and identical results
+    ref_out = {id(b): {k: v.clone() for k, v in b["out"].items()} for b in batches}
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 3))
+    t0.record(stream)
+    for _ in range(reps):
+        for b in batches:
+            b["graph"].decode(b["syndromes"], b["shot_offset"], obs_true=b["obs_true"], out=b["out"],
+                              persistent=False)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    plain = len(batches) * args.shots_per_point * reps / (t0.elapsed_time(t1) / 1e3)
+    same = all(bool((b["out"][k] == ref_out[id(b)][k]).all()) for b in batches
+               for k in ("corrections", "status", "logical_flips"))
+    tot_fail = sum(fails.values())
+    line["plain_kernel"] = {"value": plain, "unit": UNIT, "launches_per_step": len(batches),
+                            "identical_outputs": same}
+    line["ler"] = {f"{b['code']}@{b['p']}": fails[id(b)] / args.shots_per_point for b in batches}
+    line["failures_per_step"] = tot_fail
+
+    # ---- end to end through the public API with pinned host buffers
+    host = []
+    for b in batches:
+        hs = b["syndromes"].cpu().pin_memory()
+        ho = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in b["out"].items()
+              if k in ("corrections", "status", "logical_flips")}
+        host.append((b, hs, ho))
+    h2d = sum(hs.numel() * hs.element_size() for _, hs, _ in host)
+    d2h = sum(t.numel() * t.element_size() for _, _, ho in host for t in ho.values())
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        for b, hs, _ in host:
+            b["syndromes"].copy_(hs, non_blocking=True)
+        for vid, items in sorted(groups.items()):
+            pkg.decode_multi(items, stream)
+        for b, _, ho in host:
+            for k, t in ho.items():
+                t.copy_(b["out"][k], non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e = len(batches) * args.shots_per_point * args.steps / (t0.elapsed_time(t1) / 1e3)
+    line["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- request latency: seeded trace of BB72 / BB144 requests of 1..1024 shots
+    rng = np.random.default_rng(7)
+    small = [b for b in batches if b["code"] in ("bb72", "bb144") and b["p"] in (0.01, 0.05)]
+    lat = {"persistent": [], "plain": []}
+    for mode in ("plain", "persistent"):
+        per_shot = []
+        for r in range(400):
+            b = small[int(rng.integers(len(small)))]
+            n = int(rng.integers(1, 1025))
+            s0 = int(rng.integers(0, args.shots_per_point - n))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b["graph"].decode(b["syndromes"][s0:s0 + n], b["shot_offset"] + s0, persistent=(mode == "persistent"))
+            e1.record(stream)
+            e1.synchronize()
+            per_shot.append(e0.elapsed_time(e1) * 1e3)
+        lat[mode] = per_shot
+    line["latency_us"] = {m: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+                          for m, v in lat.items()}
+    line["p99_us_per_shot"] = line["latency_us"]["persistent"]["p99"]
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample of the workload
+    import oracle
+    from bpdc_inputs.sampler import sample_shots
+    oracle.build()
+    opts = oracle.Options(alpha=ALPHA, max_iter=T_ITER)
+    samples = []
+    for b in batches:
+        n = oracle_sample_plan(b["code"])
+        _, s, _ = sample_shots(b["P"], SEED, b["shot_offset"], n)
+        t = time.perf_counter()
+        oracle.decode_batch(b["P"], s, b["shot_offset"], opts)
+        samples.append((n, time.perf_counter() - t))
+    cpu = extrapolate_cpu(samples, args.shots_per_point)
+    line["cpu_baseline"] = {"value": cpu, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                            "sample": f"first {oracle_sample_plan('bb72')} (BB) / {oracle_sample_plan('hgp2500')} "
+                                      "(HGP) shots of each (code, p) point, CPU sampler, extrapolated per point "
+                                      f"to {args.shots_per_point} shots; {sum(t for _, t in samples):.1f} s of CPU"}
+
+
+if __name__ == "__main__":
+    main()

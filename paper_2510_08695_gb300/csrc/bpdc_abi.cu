@@ -533,9 +533,9 @@ int bpdc_decode(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, uint64_t s
 {
     if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
     if (B < 0) return fail(BPDC_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return BPDC_OK;
     int rc = check_outputs(out);
     if (rc != BPDC_OK) return rc;
-    if (B == 0) return BPDC_OK;
     if (!syndromes) return fail(BPDC_ERR_INVALID_ARG, "syndromes is NULL");
     std::lock_guard<std::mutex> lk(g->mu);
     DeviceGuard dgd(g->device);
@@ -553,7 +553,8 @@ int bpdc_decode_multi(const bpdc_batch *batches, int32_t n, void *stream)
         if (!batches[i].graph) return fail(BPDC_ERR_INVALID_ARG, "batch %d has no graph", i);
         if (batches[i].graph->device != dev) return fail(BPDC_ERR_INVALID_ARG, "graphs on different devices");
         if (batches[i].B < 0) return fail(BPDC_ERR_INVALID_ARG, "batch %d: B < 0", i);
-        if (batches[i].B > 0 && !batches[i].syndromes) return fail(BPDC_ERR_INVALID_ARG, "batch %d: syndromes NULL", i);
+        if (batches[i].B == 0) continue;
+        if (!batches[i].syndromes) return fail(BPDC_ERR_INVALID_ARG, "batch %d: syndromes NULL", i);
         int rc = check_outputs(&batches[i].out);
         if (rc != BPDC_OK) return rc;
     }
