@@ -107,14 +107,29 @@ def test_phenomenological_parity(pkg, oracle_mod):
     _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.8)
 
 
-def test_alpha_one_and_posterior_prior_parity(pkg, oracle_mod):
-    """Plain min-sum (alpha = 1) on uniform priors is dominated by exact ties:
-    the oracle changes outcome on ~80% of these shots under 1e-7 prior
-    perturbations, so only the well-conditioned remainder is compared."""
+def test_posterior_prior_parity(pkg, oracle_mod):
+    """Second BP on the first-run posterior (Algorithm 1 as printed)."""
     P = bi.bb_problem("bb72", 0.06)
-    for kw, frac in ((dict(ms_scale=1.0, max_iter=72), 0.1), (dict(ms_scale=0.625, max_iter=40, dc_prior=1), 0.8)):
-        g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, kw)
-        _assert_parity(P, out, ref, o, 1e-5, min_comparable=frac)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, dict(ms_scale=0.625, max_iter=40, dc_prior=1))
+    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.8)
+
+
+def test_alpha_one_parity(pkg, oracle_mod):
+    """Plain min-sum (alpha = 1) on uniform priors keeps exact symmetric ties in
+    exact-tie arithmetic; the FP64 oracle then fails twice as often as under a
+    1e-9 relative perturbation of the priors, and FP32 rounding acts like such
+    a perturbation.  Bit-exactness is required on the well-conditioned shots;
+    the failure statistics are compared with the perturbed oracle."""
+    P = bi.bb_problem("bb72", 0.06)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, dict(ms_scale=1.0, max_iter=72))
+    rep = compare(P, out, ref, o, 1e-5)
+    print({k: v for k, v in rep.items() if k != "mismatched"})
+    assert rep["comparable"] >= 0.05 * rep["B"] and len(rep["mismatched"]) == 0, rep
+    rng = np.random.default_rng(5)
+    Q = P.with_priors(P.priors * (1 + 1e-9 * rng.standard_normal(P.N)))
+    pert = oracle_mod.decode_batch(Q, s, 0, oracle_mod.Options(alpha=1.0, max_iter=72))
+    fail_p = int(((pert["status"] == 2) | (pert["obs_pred"] != o).any(1)).sum())
+    assert within_2_sigma(rep["fail_gpu"], fail_p, rep["B"]), (rep["fail_gpu"], fail_p)
 
 
 # ---------------------------------------------------------------------------
