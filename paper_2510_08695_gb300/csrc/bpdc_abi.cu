@@ -134,34 +134,43 @@ struct Packed {
     std::vector<uint32_t> thr;
 };
 
-int pack(const bpdc_graph_s &g, int G, Packed &P)
+// Packs the graph for kernel variant v; returns false if v cannot take it.
+bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
 {
+    const int G = v.G;
     const int M = g.H.rows, N = g.H.cols, K = g.L.rows, Md = g.D.rows;
     P.G = G;
     P.pc = std::max(1, (M + G - 1) / G);
     P.pv = std::max(1, (N + G - 1) / G);
     std::vector<int> deg(N, 0);
-    int dc = 0;
-    for (int i = 0; i < M; ++i) dc = std::max(dc, g.H.ptr[i + 1] - g.H.ptr[i]);
+    int dmax = 0, dmin = M > 0 ? 1 << 30 : 0;
+    for (int i = 0; i < M; ++i) {
+        const int d = g.H.ptr[i + 1] - g.H.ptr[i];
+        dmax = std::max(dmax, d);
+        dmin = std::min(dmin, d);
+    }
     for (int32_t c : g.H.col) deg[c]++;
-    int cv = 1;
-    for (int j = 0; j < N; ++j) cv = std::max(cv, deg[j]);
-    P.dc = std::max(dc, 1);
-    P.cv = cv;
+    int cmax = 0, cmin = N > 0 ? 1 << 30 : 0;
+    for (int j = 0; j < N; ++j) {
+        cmax = std::max(cmax, deg[j]);
+        cmin = std::min(cmin, deg[j]);
+    }
+    if (P.pc > v.pc_max || P.pv > v.pv_max || dmax > v.dc_max || cmax > v.cv_max) return false;
+    if (v.regular_rows && (dmin != v.dc_max || dmax != v.dc_max)) return false;
+    if (v.regular_cols && (cmin != v.cv_max || cmax != v.cv_max)) return false;
+    P.dc = std::max(dmax, 1);
+    P.cv = v.cv_max;
     const long slots = (long)P.pv * P.cv * G;
-    if (slots > 65535) return fail(BPDC_ERR_UNSUPPORTED, "graph needs %ld message slots per shot (max 65535)", slots);
+    if (slots > 65535) return false;
     P.slots = (int)slots;
     P.cmw = (P.pv * G + 31) / 32;
     P.NW = (N + 31) / 32;
     P.MW = (M + 31) / 32;
     P.KW = (K + 31) / 32;
     int region = 2 + P.slots + P.cmw + std::max(P.KW, 1);
-    if (G < 32) {
-        while (region % 32 != G % 32) ++region;   // spread the groups of a warp over the banks
-    } else {
-        region = (region + 3) & ~3;
-    }
+    region = (region + 3) & ~3;
     P.region = region;
+    if ((long)(v.block_threads / G) * region * 4 > kMaxSmemPerBlock) return false;
     // edge -> slot
     std::vector<int> fill(N, 0);
     std::vector<int> edge_slot(g.H.col.size());
@@ -188,7 +197,9 @@ int pack(const bpdc_graph_s &g, int G, Packed &P)
     for (int r = 0; r < Md; ++r) {
         for (int a = g.D.ptr[r]; a < g.D.ptr[r + 1]; ++a) {
             const int j = g.D.col[a];
-            const uint32_t s0 = (uint32_t)(((j / G) * P.cv) * G + (j % G));
+            // slot of the variable's first edge (it holds L after the last
+            // iteration); kNoEdge for a variable without edges (L = lambda)
+            const uint32_t s0 = deg[j] > 0 ? (uint32_t)(((j / G) * P.cv) * G + (j % G)) : kNoEdge;
             P.d_ent.push_back(s0 | ((uint32_t)j << 16));
         }
         P.d_ptr[r + 1] = (int32_t)P.d_ent.size();
@@ -199,15 +210,7 @@ int pack(const bpdc_graph_s &g, int G, Packed &P)
             P.l_cols[(size_t)g.L.col[a] * P.KW + (k >> 5)] |= 1u << (k & 31);
     P.thr.resize(N);
     for (int j = 0; j < N; ++j) P.thr[j] = (uint32_t)std::floor(g.priors[j] * 4294967296.0);
-    return BPDC_OK;
-}
-
-bool variant_fits(int id, const Packed &P)
-{
-    const Variant &v = variant(id);
-    if (v.G != P.G || P.pc > v.pc_max || P.dc > v.dc_max || P.pv > v.pv_max || P.cv > v.cv_max) return false;
-    const long smem = (long)(v.block_threads / v.G) * P.region * 4;
-    return smem <= kMaxSmemPerBlock;
+    return true;
 }
 
 template <typename T>
@@ -222,26 +225,21 @@ size_t put(std::vector<char> &blob, const std::vector<T> &v)
 // Packs the graph for threads_per_shot G (0 = automatic) and uploads it.
 int plan_and_upload(bpdc_graph_s *g, int want_G)
 {
-    static const int kAutoG[] = {8, 16, 32, 4, 256, 128, 512};
+    // automatic preference: one warp per shot for small graphs, then the
+    // 256- and 512-thread groups
+    static const int kOrder[] = {0, 5, 1, 3, 2, 4, 6};
     Packed P{};
     int vid = -1;
-    std::vector<int> candidates;
-    if (want_G) candidates.push_back(want_G);
-    else candidates.assign(std::begin(kAutoG), std::end(kAutoG));
-    int last_err = BPDC_OK;
-    for (int G : candidates) {
+    for (int id : kOrder) {
+        if (id >= num_variants()) continue;
+        const Variant &v = variant(id);
+        if (want_G && v.G != want_G) continue;
         Packed Q{};
-        int rc = pack(*g, G, Q);
-        if (rc != BPDC_OK) { last_err = rc; continue; }
-        for (int id = 0; id < num_variants(); ++id)
-            if (variant_fits(id, Q)) { vid = id; break; }
-        if (vid >= 0) { P = std::move(Q); break; }
+        if (pack(*g, v, Q)) { P = std::move(Q); vid = id; break; }
     }
-    if (vid < 0) {
-        if (last_err != BPDC_OK && want_G) return last_err;
+    if (vid < 0)
         return fail(BPDC_ERR_UNSUPPORTED, "no compiled kernel variant fits this graph%s",
                     want_G ? " with the requested threads per shot" : "");
-    }
     const Variant &v = variant(vid);
     const int gpb = v.block_threads / v.G;
     const int smem = gpb * P.region * 4;

@@ -78,6 +78,8 @@ struct Variant {
     int id;
     int G;
     int pc_max, dc_max, pv_max, cv_max;
+    bool regular_cols;   // every variable has exactly cv_max edges
+    bool regular_rows;   // every check has exactly dc_max edges
     int block_threads;
 };
 

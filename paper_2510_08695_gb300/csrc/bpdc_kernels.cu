@@ -137,21 +137,32 @@ __device__ __forceinline__ void cut_rows(const DevGraph &g, uint64_t gshot, int 
     }
 }
 
-template <int G, int PCM, int DCM, int PVM, int CVM>
+__device__ __forceinline__ uint32_t lds32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v));
+}
+
+// Per-lane state that depends only on the graph (reloaded when a launch
+// switches to a batch of another graph).  RV: every variable has exactly CVM
+// edges; RC: every check has exactly DCM edges.
+template <int G, int PCM, int DCM, int PVM, int CVM, bool RV, bool RC>
 struct Lane {
-    static constexpr int kIdxWords = (PCM * DCM + 1) / 2;
     static constexpr int kVmWords = (PVM * CVM + 31) / 32;
 
-    uint32_t idxw[kIdxWords];  // check slot indices, two u16 per word
-    uint32_t vm[kVmWords];     // bit (p*CVM + m): variable at pass p has an m-th edge
+    uint32_t addr[PCM * DCM];  // shared byte address of each check edge's slot (0 = no edge)
+    uint32_t vm[kVmWords];     // bit (p*CVM + m): the variable at pass p has an m-th edge
     uint32_t vvalid;           // bit p: a variable sits at pass p
-    float lamv[PVM];           // prior LLR per variable pass
+    uint32_t cvalid;           // bit p: a check sits at pass p
+    float lamv[PVM];           // prior LLR per variable pass (+inf past N)
+    uint32_t lane_base;        // shared byte address of slot(0, 0, u)
 
-    __device__ __forceinline__ uint32_t idx(int p, int k) const
-    {
-        const int n = p * DCM + k;
-        return (idxw[n >> 1] >> ((n & 1) * 16)) & 0xFFFFu;
-    }
     __device__ __forceinline__ bool has(int p, int m) const
     {
         const int n = p * CVM + m;
@@ -163,22 +174,22 @@ struct Lane {
 #pragma unroll
         for (int p = 0; p < PVM; ++p) {
             const int j = p * G + u;
-            lamv[p] = (p < g.pv && j < g.N) ? __ldg(g.lam + (size_t)p * G + u) : 0.0f;
+            lamv[p] = (p < g.pv && j < g.N) ? __ldg(g.lam + (size_t)p * G + u) : f_inf();
         }
     }
 
-    __device__ void load(const DevGraph &g, int u)
+    __device__ void load(const DevGraph &g, int u, uint32_t slot_base)
     {
-#pragma unroll
-        for (int w = 0; w < kIdxWords; ++w) idxw[w] = 0xFFFFFFFFu;
+        lane_base = slot_base + 4u * (uint32_t)u;
+        cvalid = 0;
 #pragma unroll
         for (int p = 0; p < PCM; ++p) {
+            if (p < g.pc && p * G + u < g.M) cvalid |= 1u << p;
 #pragma unroll
             for (int k = 0; k < DCM; ++k) {
                 uint32_t v = kNoEdge;
                 if (p < g.pc && k < g.dc) v = __ldg(g.chk_idx + ((size_t)p * g.dc + k) * G + u);
-                const int n = p * DCM + k;
-                idxw[n >> 1] = (idxw[n >> 1] & ~(0xFFFFu << ((n & 1) * 16))) | (v << ((n & 1) * 16));
+                addr[p * DCM + k] = (v == kNoEdge) ? 0u : slot_base + 4u * v;
             }
         }
 #pragma unroll
@@ -186,61 +197,56 @@ struct Lane {
         vvalid = 0;
 #pragma unroll
         for (int p = 0; p < PVM; ++p) {
+            const int j = p * G + u;
             int deg = 0;
-            float lam = 0.0f;
-            if (p < g.pv) {
-                const int j = p * G + u;
-                if (j < g.N) {
-                    deg = __ldg(g.var_deg + (size_t)p * G + u);
-                    lam = __ldg(g.lam + (size_t)p * G + u);
-                    vvalid |= 1u << p;
-                }
+            if (p < g.pv && j < g.N) {
+                deg = __ldg(g.var_deg + (size_t)p * G + u);
+                vvalid |= 1u << p;
             }
-            lamv[p] = lam;
 #pragma unroll
             for (int m = 0; m < CVM; ++m) {
                 const int n = p * CVM + m;
                 if (m < deg) vm[n >> 5] |= 1u << (n & 31);
             }
         }
+        reload_lam(g, u);
     }
 };
 
-template <int G, int PCM, int DCM, int PVM, int CVM>
+template <int G, int PCM, int DCM, int PVM, int CVM, bool RV, bool RC>
 struct Decoder {
-    using L = Lane<G, PCM, DCM, PVM, CVM>;
+    using L = Lane<G, PCM, DCM, PVM, CVM, RV, RC>;
+    static constexpr uint32_t kPass = 4u * CVM * G;   // bytes between variable passes
+    static constexpr uint32_t kSlot = 4u * G;         // bytes between a variable's slots
 
-    // Writes the initial messages of a BP run: every variable announces its
-    // prior (tagged with its hard decision); cut variables announce +inf.
-    // Returns the hard-decision bits per pass.
-    static __device__ __forceinline__ uint32_t init(const DevGraph &g, const L &ln, const float *lam, uint32_t cut,
-                                    float *slot, int u, float *post_row)
+    // Initial messages of a BP run: every variable announces its prior LLR
+    // tagged with its hard decision (cut variables carry lambda = +inf);
+    // unused slots are zero.  Returns the hard-decision bits per pass.
+    static __device__ __forceinline__ uint32_t init(const DevGraph &g, const L &ln, int u, float *post_row)
     {
         uint32_t hd = 0;
 #pragma unroll
         for (int p = 0; p < PVM; ++p) {
-            if (p < g.pv && ((ln.vvalid >> p) & 1u)) {
-                const uint32_t c = (cut >> p) & 1u;
-                const uint32_t e = (!c && lam[p] <= 0.0f) ? 1u : 0u;
+            if (p < g.pv) {
+                const float lam = ln.lamv[p];
+                const uint32_t e = lam <= 0.0f ? 1u : 0u;
                 hd |= e << p;
-                const float v = c ? f_inf() : tag(lam[p], e);
-                const int base = p * g.cv * G + u;
+                const uint32_t v = (__float_as_uint(lam) & ~1u) | e;
+                const uint32_t base = ln.lane_base + p * kPass;
 #pragma unroll
-                for (int m = 0; m < CVM; ++m)
-                    if (m < g.cv && (m == 0 || ln.has(p, m))) slot[base + m * G] = v;
-                if (post_row) post_row[p * G + u] = c ? f_inf() : lam[p];
+                for (int m = 0; m < CVM; ++m) sts32(base + m * kSlot, (RV || ln.has(p, m)) ? v : 0u);
+                if (post_row && ((ln.vvalid >> p) & 1u)) post_row[p * G + u] = lam;
             }
         }
-        return hd;
+        return hd & ln.vvalid;
     }
 
     // One BP run (flooding, normalized min-sum).  The slots must hold the
-    // initial messages and be visible to the whole group.  Returns whether the
-    // hard decision reproduced the syndrome; iters = iterations used; hd =
-    // hard-decision bits per variable pass.
-    static __device__ __forceinline__ bool run(const DevGraph &g, const L &ln, const Group<G> &grp, const float *lam,
-                               uint32_t cut, uint32_t sbits, float *slot, uint32_t &hd, int &iters,
-                               float *post_row)
+    // initial messages, visible to the whole group.  Returns whether the hard
+    // decision reproduced the syndrome; iters = iterations used; hd = hard
+    // decision bits per variable pass.
+    static __device__ __forceinline__ bool run(const DevGraph &g, const L &ln, const Group<G> &grp,
+                                               uint32_t sbits, uint32_t &hd, int &iters, float *post_row)
     {
         const int u = grp.u;
         const int T = g.max_iter;
@@ -252,81 +258,78 @@ struct Decoder {
 #pragma unroll
             for (int p = 0; p < PCM; ++p) {
                 if (p < g.pc) {
+                    const bool live = (ln.cvalid >> p) & 1u;
+                    uint32_t qb[DCM];
                     float mn1 = f_inf(), mn2 = f_inf();
                     int kmin = 0;
-                    uint32_t negs = 0, par = 0;
+                    uint32_t S = ((sbits >> p) & 1u) ? 0x80000001u : 0u;
 #pragma unroll
                     for (int k = 0; k < DCM; ++k) {
-                        const uint32_t a = ln.idx(p, k);
-                        const float v = (a != kNoEdge) ? slot[a] : f_inf();
-                        const uint32_t bits = __float_as_uint(v);
-                        par ^= bits;
-                        negs |= (bits >> 31) << k;
-                        const float av = fabsf(v);
+                        const uint32_t a = ln.addr[p * DCM + k];
+                        uint32_t b = 0x7F800000u;
+                        if (RC ? live : (a != 0u)) b = lds32(a);
+                        qb[k] = b;
+                        S ^= b;   // bit 31: sign parity, bit 0: hard-decision parity
+                        const float av = __uint_as_float(b & 0x7FFFFFFFu);
                         const bool lt = av < mn1;
                         mn2 = lt ? mn1 : fminf(mn2, av);
                         mn1 = lt ? av : mn1;
                         kmin = lt ? k : kmin;
                     }
-                    const uint32_t s = (sbits >> p) & 1u;
-                    unsat |= (par & 1u) ^ s;
+                    unsat |= S;
                     if (scatter) {
-                        const uint32_t sg = s ^ (__popc(negs) & 1u);
-                        const float m1 = alpha * fminf(mn1, kLlrCap);
-                        const float m2 = alpha * fminf(mn2, kLlrCap);
+                        const uint32_t Sm = S & 0x80000000u;
+                        const uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap));
+                        const uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap));
 #pragma unroll
                         for (int k = 0; k < DCM; ++k) {
-                            const uint32_t a = ln.idx(p, k);
-                            if (a != kNoEdge) {
-                                const float mag = (k == kmin) ? m2 : m1;
-                                const uint32_t neg = sg ^ ((negs >> k) & 1u);
-                                slot[a] = __uint_as_float(__float_as_uint(mag) | (neg << 31));
-                            }
+                            const uint32_t a = ln.addr[p * DCM + k];
+                            const uint32_t out = ((k == kmin) ? m2 : m1) ^ (qb[k] & 0x80000000u) ^ Sm;
+                            if (RC ? live : (a != 0u)) sts32(a, out);
                         }
                     }
                 }
             }
-            if (!grp.any(unsat != 0)) { iters = t - 1; return true; }
+            if (!grp.any((unsat & 1u) != 0)) { iters = t - 1; return true; }
             if (t > T) { iters = T; return false; }
             // ---- variable phase ----
             const bool last = t == T;
             uint32_t nhd = 0;
 #pragma unroll
             for (int p = 0; p < PVM; ++p) {
-                if (p < g.pv && ((ln.vvalid >> p) & 1u)) {
-                    const int base = p * g.cv * G + u;
+                if (p < g.pv) {
+                    const uint32_t base = ln.lane_base + p * kPass;
                     float r[CVM];
 #pragma unroll
-                    for (int m = 0; m < CVM; ++m)
-                        r[m] = (m < g.cv && ln.has(p, m)) ? slot[base + m * G] : 0.0f;
-                    float Lp = lam[p];
+                    for (int m = 0; m < CVM; ++m) r[m] = __uint_as_float(lds32(base + m * kSlot));
+                    float pre[CVM + 1];
+                    pre[0] = ln.lamv[p];
 #pragma unroll
-                    for (int m = 0; m < CVM; ++m) Lp += r[m];
-                    const uint32_t c = (cut >> p) & 1u;
-                    const uint32_t e = (!c && Lp <= 0.0f) ? 1u : 0u;
+                    for (int m = 0; m < CVM; ++m) pre[m + 1] = pre[m] + r[m];
+                    float suf[CVM + 1];
+                    suf[CVM] = 0.0f;
+                    suf[CVM - 1] = r[CVM - 1];
+#pragma unroll
+                    for (int m = CVM - 2; m >= 1; --m) suf[m] = r[m] + suf[m + 1];
+                    const float Lp = pre[CVM];
+                    const uint32_t e = Lp <= 0.0f ? 1u : 0u;
                     nhd |= e << p;
 #pragma unroll
                     for (int m = 0; m < CVM; ++m) {
-                        if (m < g.cv && (ln.has(p, m) || (last && m == 0))) {
-                            float q = lam[p];
-#pragma unroll
-                            for (int m2 = 0; m2 < CVM; ++m2)
-                                if (m2 != m) q += r[m2];
-                            if (last && m == 0) q = Lp;
-                            slot[base + m * G] = c ? f_inf() : tag(q, e);
-                        }
+                        float q = (m == CVM - 1) ? pre[m] : pre[m] + suf[m + 1];
+                        if (m == 0 && last) q = Lp;
+                        if (RV || ln.has(p, m)) sts32(base + m * kSlot, (__float_as_uint(q) & ~1u) | e);
                     }
-                    if (post_row) post_row[p * G + u] = c ? f_inf() : Lp;
+                    if (post_row && ((ln.vvalid >> p) & 1u)) post_row[p * G + u] = Lp;
                 }
             }
-            hd = nhd;
+            hd = nhd & ln.vvalid;
             grp.sync();
         }
     }
 
     static __device__ void decode(const LaunchDesc &ld, uint32_t *region, const Group<G> &grp, int gib)
     {
-        (void)gib;
         const int u = grp.u;
         L ln;
         const DevGraph *cur = nullptr;
@@ -338,6 +341,8 @@ struct Decoder {
         const int64_t groups_per_block = blockDim.x / G;
         bool once = false;
         bool lam_dirty = false;
+        const uint32_t slot_base = (uint32_t)__cvta_generic_to_shared(region + 2);
+        float *slot = reinterpret_cast<float *>(region + 2);
 
         while (true) {
             // ---- next shot ----
@@ -379,18 +384,21 @@ struct Decoder {
                 bend = bfirst + ld.batches[bi].B;
                 c_ptr = ld.batches[bi].counters;
                 const DevGraph *gnew = &ld.batches[bi].g;
-                if (cur == nullptr || gnew->chk_idx != cur->chk_idx) ln.load(*gnew, u);
+                if (cur == nullptr || gnew->chk_idx != cur->chk_idx || gnew->lam != cur->lam) {
+                    ln.load(*gnew, u, slot_base);
+                    lam_dirty = false;
+                }
                 cur = gnew;
             }
             const BatchDesc &bd = ld.batches[bi];
             const DevGraph g = bd.g;
             const int64_t b = w - bfirst;
             const uint64_t gshot = bd.shot_offset + (uint64_t)b;
-            float *slot = reinterpret_cast<float *>(region + 2);
             uint32_t *cm = region + 2 + g.slots;     // cut mask, then e_hat staging
             uint32_t *ls = cm + g.cmw;               // logical-flip staging
             float *post_row = bd.post ? bd.post + (size_t)b * g.N : nullptr;
             const uint32_t *cut_in = bd.cut_in;
+            if (lam_dirty) { ln.reload_lam(g, u); lam_dirty = false; }
 
             // ---- a1: syndrome bits of my checks ----
             uint32_t sbits = 0;
@@ -402,17 +410,19 @@ struct Decoder {
             }
             const bool nonzero = grp.any(sbits != 0);
 
-            uint32_t hd = 0, cut = 0;
+            uint32_t hd = 0;
             int st = 0, it1 = 0, it2 = 0;
             bool ran_dc = false;
-            if (lam_dirty) { ln.reload_lam(g, u); lam_dirty = false; }
             if (cut_in) {
-                // BP on a given cut graph (Algorithm 2 form), no DC
+                // BP on a given cut graph (Algorithm 2 form), no DC: cut priors -> +inf
                 const uint32_t *ci = cut_in + (size_t)b * g.NW;
 #pragma unroll
                 for (int p = 0; p < PVM; ++p) {
                     const int j = p * G + u;
-                    if (p < g.pv && j < g.N) cut |= ((__ldg(ci + (j >> 5)) >> (j & 31)) & 1u) << p;
+                    if (p < g.pv && j < g.N && ((__ldg(ci + (j >> 5)) >> (j & 31)) & 1u)) {
+                        ln.lamv[p] = f_inf();
+                        lam_dirty = true;
+                    }
                 }
             }
             if (!cut_in && !nonzero && g.zero_ok) {
@@ -424,10 +434,10 @@ struct Decoder {
                 }
             } else {
                 for (bool second = false;; second = true) {
-                    hd = init(g, ln, ln.lamv, cut, slot, u, post_row);
+                    hd = init(g, ln, u, post_row);
                     grp.sync();
                     int iters = 0;
-                    const bool ok = run(g, ln, grp, ln.lamv, cut, sbits, slot, hd, iters, post_row);
+                    const bool ok = run(g, ln, grp, sbits, hd, iters, post_row);
                     if (second) it2 = iters; else it1 = iters;
                     if (ok) { st = second ? 1 : 0; break; }
                     if (second || cut_in || !g.dc_enable) { st = 2; break; }
@@ -435,22 +445,24 @@ struct Decoder {
                     ran_dc = true;
                     for (int x = u; x < g.cmw; x += G) cm[x] = 0;
                     grp.sync();
-                    cut_rows(g, gshot, u, G, cm, [&](uint32_t s0, uint32_t) { return slot[s0]; });
+                    cut_rows(g, gshot, u, G, cm, [&](uint32_t s0, uint32_t col) {
+                        return s0 == kNoEdge ? __ldg(g.lam + col) : slot[s0];
+                    });
                     grp.sync();
 #pragma unroll
                     for (int p = 0; p < PVM; ++p) {
                         const int j = p * G + u;
                         if (p < g.pv && ((ln.vvalid >> p) & 1u)) {
-                            cut |= ((cm[j >> 5] >> (j & 31)) & 1u) << p;
-                            if (g.dc_prior) {
+                            if ((cm[j >> 5] >> (j & 31)) & 1u) {
+                                ln.lamv[p] = f_inf();   // Algorithm 2: cut prior 0
+                            } else if (g.dc_prior && ln.has(p, 0)) {
                                 // first-run posterior as prior, p_hat clamped to [1e-12, 1/2]
-                                const float Lj =
-                                    __uint_as_float(__float_as_uint(slot[p * g.cv * G + u]) & ~1u);
+                                const float Lj = __uint_as_float(__float_as_uint(slot[p * g.cv * G + u]) & ~1u);
                                 ln.lamv[p] = fminf(fmaxf(Lj, 0.0f), 27.631021115928547f);
-                                lam_dirty = true;
                             }
                         }
                     }
+                    lam_dirty = true;
                     grp.sync();
                     // ---- a8: BP again on the cut graph ----
                 }
@@ -509,7 +521,7 @@ struct Decoder {
     }
 };
 
-template <int G, int PCM, int DCM, int PVM, int CVM, int BLOCK, int MINB>
+template <int G, int PCM, int DCM, int PVM, int CVM, bool RV, bool RC, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int region_words)
 {
     extern __shared__ uint32_t smem[];
@@ -528,7 +540,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int 
         grp.leader = 0;
     }
     uint32_t *region = smem + (size_t)gib * region_words;
-    Decoder<G, PCM, DCM, PVM, CVM>::decode(ld, region, grp, gib);
+    Decoder<G, PCM, DCM, PVM, CVM, RV, RC>::decode(ld, region, grp, gib);
 }
 
 // Cut selection alone, one block per shot (same selection code as the fused kernel).
@@ -596,18 +608,19 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
 // ---------------------------------------------------------------------------
 // Variant table: (id, G, checks passes, row weight, variable passes, slots per
 // variable, block threads).
-#define BPDC_VARIANTS(X)                \
-    X(0, 8, 9, 6, 18, 3, 256, 3)        \
-    X(1, 16, 5, 6, 9, 3, 256, 3)        \
-    X(2, 32, 3, 6, 5, 3, 256, 3)        \
-    X(3, 4, 9, 6, 18, 3, 256, 3)        \
-    X(4, 256, 5, 8, 11, 4, 256, 3)      \
-    X(5, 512, 3, 8, 6, 4, 512, 2)       \
-    X(6, 128, 10, 8, 22, 4, 128, 6)     \
-    X(7, 8, 9, 8, 18, 4, 256, 3)
+// (id, G, check passes, row weight, variable passes, column weight, regular
+// columns, regular rows, block threads, min blocks per SM)
+#define BPDC_VARIANTS(X)                                 \
+    X(0, 32, 3, 6, 5, 3, true, true, 256, 4)             \
+    X(1, 256, 5, 7, 10, 4, false, true, 256, 3)          \
+    X(2, 512, 3, 7, 5, 4, false, true, 512, 2)           \
+    X(3, 256, 4, 8, 11, 3, false, false, 256, 3)         \
+    X(4, 512, 2, 8, 6, 3, false, false, 512, 2)          \
+    X(5, 32, 4, 8, 8, 4, false, false, 256, 4)           \
+    X(6, 128, 10, 7, 20, 4, false, true, 128, 6)
 
 static const Variant kVariants[] = {
-#define X(id, G, PC, DC, PV, CV, BLK, MB) {id, G, PC, DC, PV, CV, BLK},
+#define X(id, G, PC, DC, PV, CV, RV, RC, BLK, MB) {id, G, PC, DC, PV, CV, RV, RC, BLK},
     BPDC_VARIANTS(X)
 #undef X
 };
@@ -618,8 +631,8 @@ const Variant &variant(int id) { return kVariants[id]; }
 static const void *variant_fn(int id)
 {
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, BLK, MB) \
-    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, BLK, MB>;
+#define X(id, G, PC, DC, PV, CV, RV, RC, BLK, MB) \
+    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, RV, RC, BLK, MB>;
         BPDC_VARIANTS(X)
 #undef X
     default: return nullptr;
@@ -644,9 +657,9 @@ cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_byte
 {
     const int region = smem_bytes / 4 / (kVariants[id].block_threads / kVariants[id].G);
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, BLK, MB)                                                     \
-    case id:                                                                                  \
-        decode_kernel<G, PC, DC, PV, CV, BLK, MB><<<grid, BLK, smem_bytes, s>>>(ld, region); \
+#define X(id, G, PC, DC, PV, CV, RV, RC, BLK, MB)                                                     \
+    case id:                                                                                          \
+        decode_kernel<G, PC, DC, PV, CV, RV, RC, BLK, MB><<<grid, BLK, smem_bytes, s>>>(ld, region); \
         return cudaGetLastError();
         BPDC_VARIANTS(X)
 #undef X
