@@ -173,6 +173,27 @@ typedef struct {
  * on each batch.  Asynchronous on `stream`. */
 int bpdc_decode_multi(const bpdc_batch *batches, int32_t n_batches, void *stream);
 
+/* Allocation-free variant of bpdc_decode_multi (the paper has no counterpart:
+ * this is an integration aid).  Some callers cannot allocate device memory
+ * while they decode: a real-time decoding loop that must not stall on the
+ * allocator, code embedded in a host framework whose allocator owns all device
+ * memory, or a stream that is being captured into a CUDA graph.  This call
+ * allocates nothing: the persistent kernel's scratch (its device work counter
+ * and the descriptors of up to 16 batches, about 5 KB) lives in a fixed device
+ * array of the library, which every GPU that loads the library holds until the
+ * process exits.  The caller still passes every input and output, and the
+ * graphs must already exist.
+ *   - At most 16 batches per call, all on graphs that use the same kernel
+ *     variant (bpdc_graph_info.kernel_id); otherwise BPDC_ERR_UNSUPPORTED with
+ *     a message, and nothing is launched.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture on that device.
+ *   - Every call reuses the same array (the work counter is cleared at the
+ *     start of each call).  Calls whose launches overlap on the GPU, e.g. on
+ *     two streams, race on it: keep such calls ordered on one stream.
+ * Results equal those of bpdc_decode_multi on the same batches. */
+int bpdc_decode_multi_noalloc(const bpdc_batch *batches, int32_t n_batches, void *stream);
+
 /* Cut selection alone (lines 4-7 of Algorithm 1) from given posterior LLRs:
  * posterior_llr device [B][N] floats, cut_out device [B][ceil(N/32)] bits.
  * Uses the graph's D, tie_rel and tie_seed. */

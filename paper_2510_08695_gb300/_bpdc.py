@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
         "bpdc_graph_set_plan": (ctypes.c_int, [vp, i32]),
         "bpdc_decode": (ctypes.c_int, [vp, i64, vp, u64, ctypes.POINTER(_Outputs), ctypes.c_int, vp]),
         "bpdc_decode_multi": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
+        "bpdc_decode_multi_noalloc": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
         "bpdc_cut_select": (ctypes.c_int, [vp, i64, vp, u64, vp, vp]),
         "bpdc_sample": (ctypes.c_int, [vp, i64, u64, u64, vp, vp, vp, vp]),
         "bpdc_graph_sync_status": (ctypes.c_int, [vp, vp]),
@@ -262,13 +263,7 @@ class Graph:
         _check(_lib.bpdc_graph_sync_status(self.handle, _stream_ptr(stream)))
 
 
-def decode_multi(items, stream=None):
-    """Decodes several batches (possibly of different graphs) in persistent launches.
-
-    ``items``: list of dicts with keys graph, syndromes, shot_offset, out and
-    optionally obs_true, counters.
-    """
-    lib = load()
+def _batches(items):
     arr = (_Batch * len(items))()
     for i, it in enumerate(items):
         g = it["graph"]
@@ -277,7 +272,26 @@ def decode_multi(items, stream=None):
         arr[i].syndromes = it["syndromes"].data_ptr()
         arr[i].shot_offset = int(it.get("shot_offset", 0))
         arr[i].out = g._outputs(it["out"], it.get("obs_true"), it.get("counters"), it.get("cut_in"))
-    _check(lib.bpdc_decode_multi(arr, len(items), _stream_ptr(stream)))
+    return arr
+
+
+def decode_multi(items, stream=None):
+    """Decodes several batches (possibly of different graphs) in persistent launches.
+
+    ``items``: list of dicts with keys graph, syndromes, shot_offset, out and
+    optionally obs_true, counters.
+    """
+    lib = load()
+    _check(lib.bpdc_decode_multi(_batches(items), len(items), _stream_ptr(stream)))
+
+
+def decode_multi_noalloc(items, stream=None):
+    """bpdc_decode_multi_noalloc: the same decode with the library's fixed
+    device scratch (no allocation in the call); at most 16 batches, all on one
+    kernel variant.  The output tensors in ``items`` must be allocated by the
+    caller beforehand."""
+    lib = load()
+    _check(lib.bpdc_decode_multi_noalloc(_batches(items), len(items), _stream_ptr(stream)))
 
 
 def decode_backward(graph: Graph, *args, **kw):

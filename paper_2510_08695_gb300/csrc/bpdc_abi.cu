@@ -588,6 +588,53 @@ int bpdc_decode_multi(const bpdc_batch *batches, int32_t n, void *stream)
     return BPDC_OK;
 }
 
+int bpdc_decode_multi_noalloc(const bpdc_batch *batches, int32_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && !batches)) return fail(BPDC_ERR_INVALID_ARG, "bad batch list");
+    if (n == 0) return BPDC_OK;
+    if (n > kStaticBatches)
+        return fail(BPDC_ERR_UNSUPPORTED, "bpdc_decode_multi_noalloc takes at most %d batches per call (got %d)",
+                    kStaticBatches, n);
+    const int dev = batches[0].graph ? batches[0].graph->device : -1;
+    int vid = -1;
+    for (int i = 0; i < n; ++i) {
+        if (!batches[i].graph) return fail(BPDC_ERR_INVALID_ARG, "batch %d has no graph", i);
+        if (batches[i].graph->device != dev) return fail(BPDC_ERR_INVALID_ARG, "graphs on different devices");
+        if (batches[i].B < 0) return fail(BPDC_ERR_INVALID_ARG, "batch %d: B < 0", i);
+        if (vid < 0) vid = batches[i].graph->variant;
+        if (batches[i].graph->variant != vid)
+            return fail(BPDC_ERR_UNSUPPORTED, "bpdc_decode_multi_noalloc needs every graph on one kernel variant");
+        if (batches[i].B == 0) continue;
+        if (!batches[i].syndromes) return fail(BPDC_ERR_INVALID_ARG, "batch %d: syndromes NULL", i);
+        int rc = check_outputs(&batches[i].out);
+        if (rc != BPDC_OK) return rc;
+    }
+    bpdc_graph_s *owner = batches[0].graph;
+    std::lock_guard<std::mutex> lk(owner->mu);
+    DeviceGuard dgd(dev);
+    if (!dgd.ok) return fail(BPDC_ERR_CUDA, "cannot select device %d", dev);
+    BatchDesc descs[kStaticBatches];   // host stack: no allocation
+    int cnt = 0, smem = 0, bps = 0;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const bpdc_batch &bt = batches[i];
+        if (bt.B == 0) continue;
+        fill_desc(descs[cnt], bt.graph, bt.B, bt.syndromes, bt.shot_offset, &bt.out, total);
+        total += bt.B;
+        if (bt.graph->smem_bytes >= smem) {
+            smem = bt.graph->smem_bytes;
+            bps = bt.graph->blocks_per_sm;
+        }
+        ++cnt;
+    }
+    if (cnt == 0) return BPDC_OK;
+    const Variant &v = variant(vid);
+    const int64_t need = (total + v.block_threads / v.G - 1) / (v.block_threads / v.G);
+    const int64_t grid = std::min<int64_t>((int64_t)owner->sm_count * bps, need);
+    cudaError_t e = launch_variant_static(vid, descs, cnt, total, (int)grid, smem, (cudaStream_t)stream);
+    return e == cudaSuccess ? BPDC_OK : cuda_fail(e, "allocation-free decode launch");
+}
+
 int bpdc_cut_select(bpdc_graph_t g, int64_t B, const float *posterior_llr, uint64_t shot_offset,
                     uint32_t *cut_out, void *stream)
 {

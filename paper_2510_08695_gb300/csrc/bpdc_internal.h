@@ -89,6 +89,15 @@ const Variant &variant(int id);
 cudaError_t variant_attributes(int id, int smem_bytes, int *blocks_per_sm, int *regs);
 cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_bytes, cudaStream_t s);
 
+// Largest number of batches one allocation-free launch takes (its scratch is a
+// fixed device array).
+constexpr int kStaticBatches = 16;
+// Launch of variant `id` whose work counter and batch descriptors live in the
+// library's fixed device scratch array instead of caller- or library-allocated
+// memory.  host_descs: n <= kStaticBatches descriptors in host memory.
+cudaError_t launch_variant_static(int id, const BatchDesc *host_descs, int n, int64_t total, int grid,
+                                  int smem_bytes, cudaStream_t s);
+
 cudaError_t launch_cut_select(const DevGraph &g, int64_t B, const float *post, uint64_t shot_offset,
                               uint32_t *cut_out, cudaStream_t s);
 cudaError_t launch_sample(const DevGraph &g, int64_t B, uint64_t seed, uint64_t shot_offset,

@@ -667,6 +667,59 @@ cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_byte
     }
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free launches.  The persistent decode kernel needs a little
+// global scratch besides its inputs and outputs: the device work counter and
+// the descriptors of the batches of one launch.  bpdc_decode_multi takes it
+// from the graph's preallocated ring; the allocation-free entry point takes it
+// from this fixed array instead, which every GPU that loads the library keeps
+// until the process exits.  Every call shares it and it keeps the contents of
+// the last call; calls whose launches overlap on the GPU race on it.
+static __device__ __align__(256) unsigned char g_static_scratch[256 + kStaticBatches * sizeof(BatchDesc)];
+
+// Device address of the scratch array on the current device.  In host code
+// the symbol is only a host-side stand-in; the address comes from
+// cudaGetSymbolAddress, resolved once per device with that device current.
+static cudaError_t static_scratch_address(void **out)
+{
+    constexpr int kMaxDevices = 64;
+    static void *addr[kMaxDevices] = {};
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_variant_static(int id, const BatchDesc *host_descs, int n, int64_t total, int grid,
+                                  int smem_bytes, cudaStream_t s)
+{
+    if (n < 1 || n > kStaticBatches) return cudaErrorInvalidValue;
+    void *base = nullptr;
+    cudaError_t e = static_scratch_address(&base);
+    if (e != cudaSuccess) return e;
+    auto *work = reinterpret_cast<unsigned long long *>(base);
+    auto *descs = reinterpret_cast<BatchDesc *>(static_cast<unsigned char *>(base) + 256);
+    e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), s);   // the counter must start at zero
+    if (e != cudaSuccess) return e;
+    // host_descs is pageable: the copy has consumed it when the call returns
+    e = cudaMemcpyAsync(descs, host_descs, sizeof(BatchDesc) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    LaunchDesc ld{};
+    ld.batches = descs;
+    ld.n_batches = n;
+    ld.total = total;
+    ld.work = reinterpret_cast<unsigned int *>(work);
+    return launch_variant(id, ld, grid, smem_bytes, s);
+}
+
 cudaError_t launch_cut_select(const DevGraph &g, int64_t B, const float *post, uint64_t shot_offset,
                               uint32_t *cut_out, cudaStream_t s)
 {
