@@ -128,6 +128,16 @@ int bpdc_graph_get_info(bpdc_graph_t g, bpdc_graph_info *info);
  * compiled kernel variant fits the graph with that G. */
 int bpdc_graph_set_plan(bpdc_graph_t g, int32_t threads_per_shot);
 
+/* Number of compiled kernel variants (ids 0 .. count-1). */
+int bpdc_kernel_count(void);
+
+/* Selects compiled kernel variant `kernel_id` for the graph (the autotuner
+ * times every variant that accepts the graph).  INVALID_ARG for an id out of
+ * range, UNSUPPORTED if the variant cannot take this graph (group size, row or
+ * column weight, regularity or shared-memory limits); the previous plan stays
+ * in force on error.  Waits for in-flight decode calls on the graph. */
+int bpdc_graph_set_kernel(bpdc_graph_t g, int32_t kernel_id);
+
 /* Outputs of a decode call (device pointers; NULL where optional). */
 typedef struct {
     uint32_t *corrections;       /* required: [B][ceil(N/32)] e_hat bits (cut variables 0) */

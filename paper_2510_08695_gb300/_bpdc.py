@@ -97,6 +97,8 @@ def load(build_if_missing: bool = True):
         "bpdc_graph_destroy": (ctypes.c_int, [vp]),
         "bpdc_graph_get_info": (ctypes.c_int, [vp, ctypes.POINTER(_Info)]),
         "bpdc_graph_set_plan": (ctypes.c_int, [vp, i32]),
+        "bpdc_graph_set_kernel": (ctypes.c_int, [vp, i32]),
+        "bpdc_kernel_count": (ctypes.c_int, []),
         "bpdc_decode": (ctypes.c_int, [vp, i64, vp, u64, ctypes.POINTER(_Outputs), ctypes.c_int, vp]),
         "bpdc_decode_multi": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
         "bpdc_decode_multi_noalloc": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
@@ -188,6 +190,21 @@ class Graph:
     def set_plan(self, threads_per_shot: int):
         _check(_lib.bpdc_graph_set_plan(self.handle, int(threads_per_shot)))
         self._refresh()
+
+    def set_kernel(self, kernel_id: int):
+        _check(_lib.bpdc_graph_set_kernel(self.handle, int(kernel_id)))
+        self._refresh()
+
+    def kernels(self) -> list[int]:
+        """Kernel variants that accept this graph."""
+        cur = self.info["kernel_id"]
+        ok = []
+        for k in range(_lib.bpdc_kernel_count()):
+            if _lib.bpdc_graph_set_kernel(self.handle, k) == 0:
+                ok.append(k)
+        _check(_lib.bpdc_graph_set_kernel(self.handle, cur))
+        self._refresh()
+        return ok
 
     def close(self):
         if getattr(self, "handle", None):

@@ -167,7 +167,7 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     P.NW = (N + 31) / 32;
     P.MW = (M + 31) / 32;
     P.KW = (K + 31) / 32;
-    int region = 2 + P.slots + P.cmw + std::max(P.KW, 1);
+    int region = 12 + P.slots + P.cmw + std::max(P.KW, 1);   // 12 misc words (see the kernels)
     region = (region + 3) & ~3;
     P.region = region;
     if ((long)(v.block_threads / G) * region * 4 > kMaxSmemPerBlock) return false;
@@ -223,7 +223,7 @@ size_t put(std::vector<char> &blob, const std::vector<T> &v)
 }
 
 // Packs the graph for threads_per_shot G (0 = automatic) and uploads it.
-int plan_and_upload(bpdc_graph_s *g, int want_G)
+int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
 {
     // automatic preference: one warp per shot for small graphs, then the
     // 256- and 512-thread groups
@@ -236,6 +236,11 @@ int plan_and_upload(bpdc_graph_s *g, int want_G)
         if (want_G && v.G != want_G) continue;
         Packed Q{};
         if (pack(*g, v, Q)) { P = std::move(Q); vid = id; break; }
+    }
+    if (want_id >= 0) {
+        vid = -1;
+        Packed Q{};
+        if (want_id < num_variants() && pack(*g, variant(want_id), Q)) { P = std::move(Q); vid = want_id; }
     }
     if (vid < 0)
         return fail(BPDC_ERR_UNSUPPORTED, "no compiled kernel variant fits this graph%s",
@@ -501,12 +506,8 @@ int bpdc_graph_get_info(bpdc_graph_t g, bpdc_graph_info *info)
     return BPDC_OK;
 }
 
-int bpdc_graph_set_plan(bpdc_graph_t g, int32_t threads_per_shot)
+static int replan(bpdc_graph_t g, int want_G, int want_id)
 {
-    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
-    static const int ok[] = {0, 4, 8, 16, 32, 64, 128, 256, 512};
-    if (std::find(std::begin(ok), std::end(ok), threads_per_shot) == std::end(ok))
-        return fail(BPDC_ERR_INVALID_ARG, "threads_per_shot %d not in {0,4,...,512}", threads_per_shot);
     std::lock_guard<std::mutex> lk(g->mu);
     DeviceGuard dgd(g->device);
     // wait for launches that still read the old arena
@@ -516,7 +517,7 @@ int bpdc_graph_set_plan(bpdc_graph_t g, int32_t threads_per_shot)
     void *keep_arena = g->arena;
     const int kv = g->variant, kg = g->groups_per_block, kb = g->blocks_per_sm, ks = g->smem_bytes;
     g->arena = nullptr;
-    int rc = plan_and_upload(g, threads_per_shot);
+    int rc = plan_and_upload(g, want_G, want_id);
     if (rc != BPDC_OK) {
         g->dg = keep; g->arena = keep_arena; g->variant = kv;
         g->groups_per_block = kg; g->blocks_per_sm = kb; g->smem_bytes = ks;
@@ -524,6 +525,25 @@ int bpdc_graph_set_plan(bpdc_graph_t g, int32_t threads_per_shot)
     }
     cudaFree(keep_arena);
     return BPDC_OK;
+}
+
+int bpdc_graph_set_plan(bpdc_graph_t g, int32_t threads_per_shot)
+{
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    static const int ok[] = {0, 4, 8, 16, 32, 64, 128, 256, 512};
+    if (std::find(std::begin(ok), std::end(ok), threads_per_shot) == std::end(ok))
+        return fail(BPDC_ERR_INVALID_ARG, "threads_per_shot %d not in {0,4,...,512}", threads_per_shot);
+    return replan(g, threads_per_shot, -1);
+}
+
+int bpdc_kernel_count(void) { return num_variants(); }
+
+int bpdc_graph_set_kernel(bpdc_graph_t g, int32_t kernel_id)
+{
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    if (kernel_id < 0 || kernel_id >= num_variants())
+        return fail(BPDC_ERR_INVALID_ARG, "kernel_id %d out of range [0, %d)", kernel_id, num_variants());
+    return replan(g, 0, kernel_id);
 }
 
 int bpdc_decode(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, uint64_t shot_offset,

@@ -81,6 +81,7 @@ struct Variant {
     bool regular_cols;   // every variable has exactly cv_max edges
     bool regular_rows;   // every check has exactly dc_max edges
     int block_threads;
+    int min_blocks;      // launch bound: resident blocks per SM the register budget allows
 };
 
 int num_variants();

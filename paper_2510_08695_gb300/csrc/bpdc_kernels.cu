@@ -137,6 +137,10 @@ __device__ __forceinline__ void cut_rows(const DevGraph &g, uint64_t gshot, int 
     }
 }
 
+// Shared words at the start of every group's region: 0-1 shot broadcast
+// (double buffered), 2 the +inf word, 4-11 the per-batch counters.
+constexpr int kMiscWords = 12;
+
 __device__ __forceinline__ uint32_t lds32(uint32_t a)
 {
     uint32_t v;
@@ -156,12 +160,13 @@ template <int G, int PCM, int DCM, int PVM, int CVM, bool RV, bool RC>
 struct Lane {
     static constexpr int kVmWords = (PVM * CVM + 31) / 32;
 
-    uint32_t addr[PCM * DCM];  // shared byte address of each check edge's slot (0 = no edge)
+    uint32_t addr[PCM * DCM];  // shared byte address of each check edge's slot (the +inf word if none)
     uint32_t vm[kVmWords];     // bit (p*CVM + m): the variable at pass p has an m-th edge
     uint32_t vvalid;           // bit p: a variable sits at pass p
     uint32_t cvalid;           // bit p: a check sits at pass p
     float lamv[PVM];           // prior LLR per variable pass (+inf past N)
     uint32_t lane_base;        // shared byte address of slot(0, 0, u)
+    uint32_t inf_addr;         // shared byte address of the group's +inf word
 
     __device__ __forceinline__ bool has(int p, int m) const
     {
@@ -178,9 +183,10 @@ struct Lane {
         }
     }
 
-    __device__ void load(const DevGraph &g, int u, uint32_t slot_base)
+    __device__ void load(const DevGraph &g, int u, uint32_t slot_base, uint32_t inf_word)
     {
         lane_base = slot_base + 4u * (uint32_t)u;
+        inf_addr = inf_word;
         cvalid = 0;
 #pragma unroll
         for (int p = 0; p < PCM; ++p) {
@@ -189,7 +195,7 @@ struct Lane {
             for (int k = 0; k < DCM; ++k) {
                 uint32_t v = kNoEdge;
                 if (p < g.pc && k < g.dc) v = __ldg(g.chk_idx + ((size_t)p * g.dc + k) * G + u);
-                addr[p * DCM + k] = (v == kNoEdge) ? 0u : slot_base + 4u * v;
+                addr[p * DCM + k] = (v == kNoEdge) ? inf_word : slot_base + 4u * v;
             }
         }
 #pragma unroll
@@ -265,27 +271,25 @@ struct Decoder {
                     uint32_t S = ((sbits >> p) & 1u) ? 0x80000001u : 0u;
 #pragma unroll
                     for (int k = 0; k < DCM; ++k) {
-                        const uint32_t a = ln.addr[p * DCM + k];
-                        uint32_t b = 0x7F800000u;
-                        if (RC ? live : (a != 0u)) b = lds32(a);
+                        // unused slots point at the group's +inf word
+                        const uint32_t b = lds32(ln.addr[p * DCM + k]);
                         qb[k] = b;
                         S ^= b;   // bit 31: sign parity, bit 0: hard-decision parity
-                        const float av = __uint_as_float(b & 0x7FFFFFFFu);
-                        const bool lt = av < mn1;
-                        mn2 = lt ? mn1 : fminf(mn2, av);
-                        mn1 = lt ? av : mn1;
-                        kmin = lt ? k : kmin;
+                        const float av = fabsf(__uint_as_float(b));
+                        kmin = av < mn1 ? k : kmin;
+                        mn2 = fminf(mn2, fmaxf(mn1, av));
+                        mn1 = fminf(mn1, av);
                     }
                     unsat |= S;
                     if (scatter) {
                         const uint32_t Sm = S & 0x80000000u;
-                        const uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap));
-                        const uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap));
+                        const uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap)) ^ Sm;
+                        const uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap)) ^ Sm;
 #pragma unroll
                         for (int k = 0; k < DCM; ++k) {
                             const uint32_t a = ln.addr[p * DCM + k];
-                            const uint32_t out = ((k == kmin) ? m2 : m1) ^ (qb[k] & 0x80000000u) ^ Sm;
-                            if (RC ? live : (a != 0u)) sts32(a, out);
+                            const uint32_t out = ((k == kmin) ? m2 : m1) ^ (qb[k] & 0x80000000u);
+                            if (RC ? live : (a != ln.inf_addr)) sts32(a, out);
                         }
                     }
                 }
@@ -335,14 +339,19 @@ struct Decoder {
         const DevGraph *cur = nullptr;
         int bi = -1;
         int64_t bfirst = 0, bend = 0;
-        unsigned long long c_shots = 0, c_fail = 0, c_iters = 0, c_dc = 0;
+        // per-batch counters accumulate in the group's shared misc words 4..11
+        // (lane 0 only) and are flushed when the group moves to another batch
+        unsigned long long *cnt = reinterpret_cast<unsigned long long *>(region + 4);
         unsigned long long *c_ptr = nullptr;
+        if (u == 0) cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
         uint32_t bufsel = 0;
         const int64_t groups_per_block = blockDim.x / G;
         bool once = false;
         bool lam_dirty = false;
-        const uint32_t slot_base = (uint32_t)__cvta_generic_to_shared(region + 2);
-        float *slot = reinterpret_cast<float *>(region + 2);
+        const uint32_t slot_base = (uint32_t)__cvta_generic_to_shared(region + kMiscWords);
+        const uint32_t inf_word = (uint32_t)__cvta_generic_to_shared(region + 2);
+        float *slot = reinterpret_cast<float *>(region + kMiscWords);
+        if (u == 0) region[2] = 0x7F800000u;   // read by unused check slots
 
         while (true) {
             // ---- next shot ----
@@ -367,13 +376,11 @@ struct Decoder {
             }
             if (w >= ld.total) break;
             if (w < bfirst || w >= bend) {
-                if (c_ptr && u == 0) {
-                    atomicAdd(c_ptr + 0, c_shots);
-                    atomicAdd(c_ptr + 1, c_fail);
-                    atomicAdd(c_ptr + 2, c_iters);
-                    atomicAdd(c_ptr + 3, c_dc);
+                if (u == 0) {
+                    if (c_ptr)
+                        for (int x = 0; x < 4; ++x) atomicAdd(c_ptr + x, cnt[x]);
+                    cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
                 }
-                c_shots = c_fail = c_iters = c_dc = 0;
                 int lo = 0, hi = ld.n_batches - 1;
                 while (lo < hi) {  // last batch with first <= w
                     const int mid = (lo + hi + 1) >> 1;
@@ -385,7 +392,7 @@ struct Decoder {
                 c_ptr = ld.batches[bi].counters;
                 const DevGraph *gnew = &ld.batches[bi].g;
                 if (cur == nullptr || gnew->chk_idx != cur->chk_idx || gnew->lam != cur->lam) {
-                    ln.load(*gnew, u, slot_base);
+                    ln.load(*gnew, u, slot_base, inf_word);
                     lam_dirty = false;
                 }
                 cur = gnew;
@@ -394,7 +401,7 @@ struct Decoder {
             const DevGraph g = bd.g;
             const int64_t b = w - bfirst;
             const uint64_t gshot = bd.shot_offset + (uint64_t)b;
-            uint32_t *cm = region + 2 + g.slots;     // cut mask, then e_hat staging
+            uint32_t *cm = region + kMiscWords + g.slots;   // cut mask, then e_hat staging
             uint32_t *ls = cm + g.cmw;               // logical-flip staging
             float *post_row = bd.post ? bd.post + (size_t)b * g.N : nullptr;
             const uint32_t *cut_in = bd.cut_in;
@@ -506,18 +513,14 @@ struct Decoder {
             if (u == 0) {
                 bd.status[b] = (uint8_t)st;
                 if (bd.iters) bd.iters[b] = (uint32_t)it1 | ((uint32_t)it2 << 16);
+                cnt[0] += 1;
+                cnt[1] += fail ? 1 : 0;
+                cnt[2] += (unsigned long long)(it1 + it2);
+                cnt[3] += ran_dc ? 1 : 0;
             }
-            c_shots += 1;
-            c_fail += fail ? 1 : 0;
-            c_iters += (unsigned long long)(it1 + it2);
-            c_dc += ran_dc ? 1 : 0;
         }
-        if (c_ptr && u == 0) {
-            atomicAdd(c_ptr + 0, c_shots);
-            atomicAdd(c_ptr + 1, c_fail);
-            atomicAdd(c_ptr + 2, c_iters);
-            atomicAdd(c_ptr + 3, c_dc);
-        }
+        if (c_ptr && u == 0)
+            for (int x = 0; x < 4; ++x) atomicAdd(c_ptr + x, cnt[x]);
     }
 };
 
@@ -617,10 +620,14 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
     X(3, 256, 4, 8, 11, 3, false, false, 256, 3)         \
     X(4, 512, 2, 8, 6, 3, false, false, 512, 2)          \
     X(5, 32, 4, 8, 8, 4, false, false, 256, 4)           \
-    X(6, 128, 10, 7, 20, 4, false, true, 128, 6)
+    X(6, 128, 10, 7, 20, 4, false, true, 128, 6)         \
+    X(7, 32, 3, 6, 5, 3, true, true, 256, 3)             \
+    X(8, 256, 5, 7, 10, 4, false, true, 256, 2)          \
+    X(9, 512, 3, 7, 5, 4, false, true, 512, 1)           \
+    X(10, 256, 4, 8, 11, 3, false, false, 256, 2)
 
 static const Variant kVariants[] = {
-#define X(id, G, PC, DC, PV, CV, RV, RC, BLK, MB) {id, G, PC, DC, PV, CV, RV, RC, BLK},
+#define X(id, G, PC, DC, PV, CV, RV, RC, BLK, MB) {id, G, PC, DC, PV, CV, RV, RC, BLK, MB},
     BPDC_VARIANTS(X)
 #undef X
 };
