@@ -50,11 +50,15 @@ def shard_offset(rank: int, shots_per_point: int) -> int:
     return rank * shots_per_point
 
 
-def workload_problems():
+def workload_problems(only=None, p_only=None):
     import bpdc_inputs as bi
     probs = []
     for code in CODES:
+        if only and code != only:
+            continue
         for p in P_VALUES:
+            if p_only is not None and abs(p - p_only) > 1e-9:
+                continue
             if code == "hgp2500":
                 probs.append((code, p, bi.hgp_problem(p)))
             else:
@@ -161,11 +165,14 @@ def run_reference(args, world, rank):
 
 
 def config_dict(args, world):
+    n_points = len(workload_problems(getattr(args, "only", None), getattr(args, "p", None)))
+    restricted = "" if n_points == len(CODES) * len(P_VALUES) else \
+        f" [restricted to code={getattr(args, 'only', None)} p={getattr(args, 'p', None)}]"
     return {"workload": "batched code capacity across uneven codes: BB[[144,12,12]], BB[[72,12,6]], "
                         "HGP of a seeded (3,4)-regular n=40 code (n=2500, k=148); p=0.01..0.10 (10 values); "
                         f"{args.shots_per_point} shots per (code,p) per GPU; normalized min-sum alpha=0.625, "
-                        "T_iter=50, DC on failure, second BP on priors p",
-            "shots_per_step": len(CODES) * len(P_VALUES) * args.shots_per_point * world,
+                        "T_iter=50, DC on failure, second BP on priors p" + restricted,
+            "shots_per_step": n_points * args.shots_per_point * world,
             "launch": "persistent multi-batch launches (one per kernel variant), device work counter",
             "l2": "inputs larger than L2 (no flush)",
             "parallelism": f"dp{world}"}
@@ -179,6 +186,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shots-per-point", type=int, default=1_000_000)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/latency/cpu legs")
+    ap.add_argument("--only", choices=CODES, default=None,
+                    help="restrict the workload to one code (small profiling cases; not a bench line)")
+    ap.add_argument("--p", type=float, default=None, help="restrict the workload to one error rate")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -205,7 +215,7 @@ def main():
 
     spp = args.shots_per_point
     off = shard_offset(rank, spp)
-    probs = workload_problems()
+    probs = workload_problems(args.only, args.p)
     opts = pkg.Options(ms_scale=ALPHA, max_iter=T_ITER)
     batches = []
     for code, p, P in probs:
@@ -261,6 +271,10 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     shots_per_step = len(batches) * spp * world
+    if args.only or args.p is not None:
+        line_note = "restricted workload (profiling case)"
+    else:
+        line_note = None
     value = shots_per_step * args.steps / (ms / 1e3)
 
     # dominant launch: per-variant average duration and algorithmic bytes
@@ -290,6 +304,7 @@ def main():
                          "algorithmic_bytes": f"{EDGE_UPDATE_BYTES} B per edge-update x "
                                               f"{dom['edge_updates']} edge-updates per launch"},
             "per_variant_ms": {str(v["kernel_id"]): round(v["ms"], 3) for v in per_variant},
+            "note": line_note,
             "gpu_launches": args.steps * len(groups),
             "clocks": clk}
 

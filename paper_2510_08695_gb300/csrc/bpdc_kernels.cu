@@ -39,6 +39,9 @@
 // winner's bit in a shared cut mask; BP runs again with cut variables pinned
 // to +inf and the priors of Sec. III.B.
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cuda_runtime.h>
 
 #include "bpdc_internal.h"
@@ -646,18 +649,42 @@ static const void *variant_fn(int id)
     }
 }
 
+// Occupancy of a variant at a shared-memory size, cached per device.  The
+// dynamic shared-memory limit of a kernel only ever grows, so a smaller graph
+// created later never lowers it under a larger one that is still in use.
 cudaError_t variant_attributes(int id, int smem_bytes, int *blocks_per_sm, int *regs)
 {
     const void *fn = variant_fn(id);
     if (!fn) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, std::pair<int, int>> cache;   // (dev, id, smem) -> (bps, regs)
+    static std::map<std::pair<int, int>, int> limit;                         // (dev, id) -> smem limit set
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(std::make_tuple(dev, id, smem_bytes));
+    if (it != cache.end()) {
+        *blocks_per_sm = it->second.first;
+        if (regs) *regs = it->second.second;
+        return cudaSuccess;
+    }
+    int &lim = limit[std::make_pair(dev, id)];
+    if (smem_bytes > lim) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e != cudaSuccess) return e;
+        lim = smem_bytes;
+    }
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return e;
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kVariants[id].block_threads, smem_bytes);
+    if (e != cudaSuccess) return e;
+    cache[std::make_tuple(dev, id, smem_bytes)] = std::make_pair(bps, (int)fa.numRegs);
+    *blocks_per_sm = bps;
     if (regs) *regs = fa.numRegs;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kVariants[id].block_threads,
-                                                         smem_bytes);
+    return cudaSuccess;
 }
 
 cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_bytes, cudaStream_t s)
