@@ -76,6 +76,32 @@ def oracle_sample_plan(code: str) -> int:
     return 400 if code == "hgp2500" else 4000
 
 
+def profiled_traffic(kernel_id: int, shots: int, edge_updates: int):
+    """DRAM bytes per launch of a kernel variant, scaled from its committed ncu
+    summary (profiles/decode_kernel_*.md) by the shots the launch processes
+    (DRAM traffic is syndromes in, corrections out: it grows with shots, not
+    iterations), plus the shared-memory wavefront bytes scaled by
+    edge-updates.  (None, None) if no summary matches the current kernel
+    source."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_2510_08695_gb300", "csrc", "bpdc_kernels.cu")
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "decode_kernel_*.md"))):
+        text = open(path).read()
+        if f"# decode_kernel variant {kernel_id} " not in text:
+            continue
+        kv = dict(line.split(": ", 1) for line in text.splitlines()
+                  if ": " in line and line.split(": ", 1)[0] in
+                  ("traffic_bytes_per_shot", "smem_wavefront_bytes_per_edge_update", "kernel_source_sha256_16"))
+        if kv.get("kernel_source_sha256_16") != cur or "traffic_bytes_per_shot" not in kv:
+            return None, None, os.path.basename(path)
+        smem = float(kv["smem_wavefront_bytes_per_edge_update"]) * edge_updates \
+            if "smem_wavefront_bytes_per_edge_update" in kv else None
+        return float(kv["traffic_bytes_per_shot"]) * shots, smem, os.path.basename(path)
+    return None, None, None
+
+
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
@@ -282,13 +308,15 @@ def main():
     for gi, (vid, items) in enumerate(sorted(groups.items())):
         d_ms = statistics.mean(ev[k][gi][0].elapsed_time(ev[k][gi][1]) for k in range(args.steps))
         eu = sum(iters[id(b)] * b["graph"].E for b in items)
-        per_variant.append(dict(kernel_id=vid, ms=d_ms, edge_updates=eu, codes=sorted({b["code"] for b in items})))
+        per_variant.append(dict(kernel_id=vid, ms=d_ms, edge_updates=eu, codes=sorted({b["code"] for b in items}),
+                                shots=len(items) * spp))
     dom = max(per_variant, key=lambda v: v["ms"])
     sm_mhz = clk.get("sm_mhz") or 2070.0
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     peak_gbs = nsm * SMEM_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9
     achieved_gbs = dom["edge_updates"] * EDGE_UPDATE_BYTES / (dom["ms"] / 1e3) / 1e9
     total_eu = sum(v["edge_updates"] for v in per_variant)
+    traffic, smem_traffic, prof_file = profiled_traffic(dom["kernel_id"], dom["shots"], dom["edge_updates"])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -297,7 +325,10 @@ def main():
             "config": config_dict(args, world),
             "edge_updates_per_s": total_eu * world / (ms / args.steps / 1e3),
             "roofline": {"bound": "smem", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
-                         "frac": achieved_gbs / peak_gbs, "traffic": None,
+                         "frac": achieved_gbs / peak_gbs, "traffic": traffic,
+                         "traffic_source": (f"DRAM bytes from profiles/{prof_file}, scaled by shots per launch"
+                                            if traffic is not None else "no ncu summary of the current kernel"),
+                         "smem_wavefront_bytes": smem_traffic,
                          "kernel": f"decode_kernel variant {dom['kernel_id']} ({'+'.join(dom['codes'])})",
                          "peak_source": f"{nsm} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x median sampled SM clock "
                                         f"{sm_mhz:.0f} MHz",
