@@ -138,6 +138,21 @@ int bpdc_kernel_count(void);
  * in force on error.  Waits for in-flight decode calls on the graph. */
 int bpdc_graph_set_kernel(bpdc_graph_t g, int32_t kernel_id);
 
+/* Message layout of the graph: 1 (the default) places variables and orders
+ * the edges of every check so that the check update's shared-memory gathers
+ * and scatters avoid bank conflicts; 0 uses the identity placement and the
+ * CSR order.  Results are identical; only the speed differs.  Keeps the
+ * kernel variant; waits for in-flight decode calls on the graph. */
+int bpdc_graph_set_layout(bpdc_graph_t g, int32_t mode);
+
+/* The layout planner alone (host only, no GPU needed): for a check matrix H
+ * and a group size G (a multiple of 32) writes the position of every variable
+ * (pos_of_var[N], positions in [0, ceil(N/G)*G), bank = pos mod 32) and the
+ * round of every edge within its check (edge_round[nnz], in H's CSR order;
+ * distinct within a check, below the maximum row weight).  optimize = 0 gives
+ * the identity placement and the CSR order. */
+int bpdc_layout_plan(const bpdc_csr *H, int32_t G, int32_t optimize, int32_t *pos_of_var, int32_t *edge_round);
+
 /* Outputs of a decode call (device pointers; NULL where optional). */
 typedef struct {
     uint32_t *corrections;       /* required: [B][ceil(N/32)] e_hat bits (cut variables 0) */

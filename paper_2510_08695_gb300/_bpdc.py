@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True):
         "bpdc_graph_set_plan": (ctypes.c_int, [vp, i32]),
         "bpdc_graph_set_kernel": (ctypes.c_int, [vp, i32]),
         "bpdc_kernel_count": (ctypes.c_int, []),
+        "bpdc_graph_set_layout": (ctypes.c_int, [vp, i32]),
+        "bpdc_layout_plan": (ctypes.c_int, [ctypes.POINTER(_Csr), i32, i32, _i32p, _i32p]),
         "bpdc_decode": (ctypes.c_int, [vp, i64, vp, u64, ctypes.POINTER(_Outputs), ctypes.c_int, vp]),
         "bpdc_decode_multi": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
         "bpdc_decode_multi_noalloc": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
@@ -189,6 +191,11 @@ class Graph:
 
     def set_plan(self, threads_per_shot: int):
         _check(_lib.bpdc_graph_set_plan(self.handle, int(threads_per_shot)))
+        self._refresh()
+
+    def set_layout(self, mode: int):
+        """1: bank-conflict-aware message layout (default); 0: identity layout."""
+        _check(_lib.bpdc_graph_set_layout(self.handle, int(mode)))
         self._refresh()
 
     def set_kernel(self, kernel_id: int):
@@ -314,6 +321,17 @@ def decode_multi_noalloc(items, stream=None):
 def decode_backward(graph: Graph, *args, **kw):
     lib = load()
     _check(lib.bpdc_decode_backward(graph.handle, 0, None, None, None, None, None))
+
+
+def layout_plan(H, G: int, optimize: bool = True):
+    """Host-only layout planner: (pos_of_var [N], edge_round [nnz] in H's CSR order)."""
+    lib = load()
+    h, keep = _csr(H)
+    pos = np.zeros(h.cols, np.int32)
+    rnd = np.zeros(max(int(h.nnz), 1), np.int32)
+    _check(lib.bpdc_layout_plan(ctypes.byref(h), int(G), int(bool(optimize)), pos.ctypes.data_as(_i32p),
+                                rnd.ctypes.data_as(_i32p)))
+    return pos, rnd[:int(h.nnz)]
 
 
 def version() -> str:

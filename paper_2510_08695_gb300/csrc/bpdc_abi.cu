@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -116,6 +117,7 @@ struct bpdc_graph_s {
     void *ring_host = nullptr;
     RingSlot ring[kRing];
     int ring_next = 0;
+    int layout = 1;   // 1: bank-conflict-aware placement, 0: identity
     std::mutex mu;
 };
 
@@ -130,8 +132,11 @@ struct Packed {
     std::vector<float> lam;
     std::vector<int32_t> d_ptr;
     std::vector<uint32_t> d_ent;
+    std::vector<int32_t> d_col;
+    std::vector<uint32_t> l_pos;
     std::vector<uint32_t> l_cols;
     std::vector<uint32_t> thr;
+    std::vector<int32_t> pos_col;
 };
 
 // Packs the graph for kernel variant v; returns false if v cannot take it.
@@ -171,43 +176,59 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     region = (region + 3) & ~3;
     P.region = region;
     if ((long)(v.block_threads / G) * region * 4 > kMaxSmemPerBlock) return false;
-    // edge -> slot
+    // variable placement and edge order (bpdc_layout.cu)
+    const int npos = P.pv * G;
+    Layout lay;
+    plan_layout(M, N, g.H.ptr, g.H.col, G, npos, P.dc, g.layout != 0, lay);
+    // edge -> slot of its variable
     std::vector<int> fill(N, 0);
     std::vector<int> edge_slot(g.H.col.size());
     for (int i = 0; i < M; ++i)
         for (int a = g.H.ptr[i]; a < g.H.ptr[i + 1]; ++a) {
             const int j = g.H.col[a];
+            const int pos = lay.pos_of_var[j];
             const int m = fill[j]++;
-            edge_slot[a] = ((j / G) * P.cv + m) * G + (j % G);
+            edge_slot[a] = ((pos / G) * P.cv + m) * G + (pos % G);
         }
     P.chk_idx.assign((size_t)P.pc * P.dc * G, kNoEdge);
     for (int i = 0; i < M; ++i) {
         const int p = i / G, u = i % G;
-        for (int a = g.H.ptr[i], k = 0; a < g.H.ptr[i + 1]; ++a, ++k)
-            P.chk_idx[((size_t)p * P.dc + k) * G + u] = (uint16_t)edge_slot[a];
+        for (int a = g.H.ptr[i]; a < g.H.ptr[i + 1]; ++a)
+            P.chk_idx[((size_t)p * P.dc + lay.edge_round[a]) * G + u] = (uint16_t)edge_slot[a];
     }
-    P.var_deg.assign((size_t)P.pv * G, 0);
-    P.lam.assign((size_t)P.pv * G, 0.0f);
+    P.var_deg.assign((size_t)npos, 0xFF);   // 0xFF: no variable at this position
+    P.lam.assign((size_t)npos, std::numeric_limits<float>::infinity());
+    P.pos_col.assign((size_t)npos, -1);
     for (int j = 0; j < N; ++j) {
-        P.var_deg[j] = (uint8_t)deg[j];   // position p*G+u == j
-        P.lam[j] = (float)std::log((1.0 - g.priors[j]) / g.priors[j]);
+        const int pos = lay.pos_of_var[j];
+        P.var_deg[pos] = (uint8_t)deg[j];
+        P.lam[pos] = (float)std::log((1.0 - g.priors[j]) / g.priors[j]);
+        P.pos_col[pos] = j;
     }
     P.d_ptr.assign(Md + 1, 0);
     P.d_ent.clear();
+    P.d_col.clear();
     for (int r = 0; r < Md; ++r) {
         for (int a = g.D.ptr[r]; a < g.D.ptr[r + 1]; ++a) {
             const int j = g.D.col[a];
+            const int pos = lay.pos_of_var[j];
             // slot of the variable's first edge (it holds L after the last
             // iteration); kNoEdge for a variable without edges (L = lambda)
-            const uint32_t s0 = deg[j] > 0 ? (uint32_t)(((j / G) * P.cv) * G + (j % G)) : kNoEdge;
-            P.d_ent.push_back(s0 | ((uint32_t)j << 16));
+            const uint32_t s0 = deg[j] > 0 ? (uint32_t)(((pos / G) * P.cv) * G + (pos % G)) : kNoEdge;
+            P.d_ent.push_back(s0 | ((uint32_t)pos << 16));
+            P.d_col.push_back(j);
         }
         P.d_ptr[r + 1] = (int32_t)P.d_ent.size();
     }
-    P.l_cols.assign((size_t)N * std::max(P.KW, 1), 0);
+    const int kw = std::max(P.KW, 1);
+    P.l_cols.assign((size_t)N * kw, 0);
+    P.l_pos.assign((size_t)npos * kw, 0);
     for (int k = 0; k < K; ++k)
-        for (int a = g.L.ptr[k]; a < g.L.ptr[k + 1]; ++a)
-            P.l_cols[(size_t)g.L.col[a] * P.KW + (k >> 5)] |= 1u << (k & 31);
+        for (int a = g.L.ptr[k]; a < g.L.ptr[k + 1]; ++a) {
+            const int j = g.L.col[a];
+            P.l_cols[(size_t)j * kw + (k >> 5)] |= 1u << (k & 31);
+            P.l_pos[(size_t)lay.pos_of_var[j] * kw + (k >> 5)] |= 1u << (k & 31);
+        }
     P.thr.resize(N);
     for (int j = 0; j < N; ++j) P.thr[j] = (uint32_t)std::floor(g.priors[j] * 4294967296.0);
     return true;
@@ -256,7 +277,8 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     // device arena
     std::vector<char> blob;
     const size_t o_chk = put(blob, P.chk_idx), o_deg = put(blob, P.var_deg), o_lam = put(blob, P.lam);
-    const size_t o_dptr = put(blob, P.d_ptr), o_dent = put(blob, P.d_ent), o_l = put(blob, P.l_cols);
+    const size_t o_dptr = put(blob, P.d_ptr), o_dent = put(blob, P.d_ent), o_l = put(blob, P.l_pos);
+    const size_t o_dcol = put(blob, P.d_col), o_lcol = put(blob, P.l_cols), o_pcol = put(blob, P.pos_col);
     const size_t o_hptr = put(blob, g->H.ptr), o_hcol = put(blob, g->H.col), o_thr = put(blob, P.thr);
     const size_t o_err = put(blob, std::vector<int32_t>(4, 0));
     void *arena = nullptr;
@@ -287,6 +309,9 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     d.d_ptr = (const int32_t *)(base + o_dptr);
     d.d_ent = (const uint32_t *)(base + o_dent);
     d.l_bits = (const uint32_t *)(base + o_l);
+    d.d_col = (const int32_t *)(base + o_dcol);
+    d.l_col = (const uint32_t *)(base + o_lcol);
+    d.pos_col = (const int32_t *)(base + o_pcol);
     d.h_ptr = (const int32_t *)(base + o_hptr);
     d.h_col = (const int32_t *)(base + o_hcol);
     d.thr = (const uint32_t *)(base + o_thr);
@@ -537,6 +562,40 @@ int bpdc_graph_set_plan(bpdc_graph_t g, int32_t threads_per_shot)
 }
 
 int bpdc_kernel_count(void) { return num_variants(); }
+
+int bpdc_layout_plan(const bpdc_csr *H, int32_t G, int32_t optimize, int32_t *pos_of_var, int32_t *edge_round)
+{
+    HostCsr h;
+    int rc = copy_csr(H, "H", h);
+    if (rc != BPDC_OK) return rc;
+    if (G < 32 || G % 32 != 0 || G > 1024) return fail(BPDC_ERR_INVALID_ARG, "G must be a multiple of 32 in [32, 1024]");
+    if (!pos_of_var || !edge_round) return fail(BPDC_ERR_INVALID_ARG, "NULL output");
+    int dc = 1;
+    for (int i = 0; i < h.rows; ++i) dc = std::max(dc, h.ptr[i + 1] - h.ptr[i]);
+    const int npos = std::max(1, (h.cols + G - 1) / G) * G;
+    Layout lay;
+    plan_layout(h.rows, h.cols, h.ptr, h.col, G, npos, dc, optimize != 0, lay);
+    std::copy(lay.pos_of_var.begin(), lay.pos_of_var.end(), pos_of_var);
+    // edge_round is reported in the caller's CSR order (copy_csr sorted each row)
+    for (int i = 0; i < h.rows; ++i)
+        for (int a = H->row_ptr[i]; a < H->row_ptr[i + 1]; ++a) {
+            const int c = H->col_idx[a];
+            const int b = (int)(std::lower_bound(h.col.begin() + h.ptr[i], h.col.begin() + h.ptr[i + 1], c) - h.col.begin());
+            edge_round[a] = lay.edge_round[b];
+        }
+    return BPDC_OK;
+}
+
+int bpdc_graph_set_layout(bpdc_graph_t g, int32_t mode)
+{
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    if (mode != 0 && mode != 1) return fail(BPDC_ERR_INVALID_ARG, "layout mode must be 0 or 1");
+    const int keep = g->layout;
+    g->layout = mode;
+    const int rc = replan(g, 0, g->variant);
+    if (rc != BPDC_OK) g->layout = keep;
+    return rc;
+}
 
 int bpdc_graph_set_kernel(bpdc_graph_t g, int32_t kernel_id)
 {

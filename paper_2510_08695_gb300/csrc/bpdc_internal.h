@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace bpdc {
@@ -41,8 +42,11 @@ struct DevGraph {
     const uint8_t *var_deg;      // [pv][G] degree of the variable (0 past N)
     const float *lam;            // [pv][G] prior LLR ln((1-p)/p)
     const int32_t *d_ptr;        // [Md+1] rows of D
-    const uint32_t *d_ent;       // [nnz(D)] slot of the variable's first edge | column << 16
-    const uint32_t *l_bits;      // [K][NW] rows of L as bit masks
+    const uint32_t *d_ent;       // [nnz(D)] slot of the variable's first edge | position << 16
+    const int32_t *d_col;        // [nnz(D)] column of each D entry (ascending within a row)
+    const uint32_t *l_bits;      // [pv*G][KW] columns of L by variable position
+    const uint32_t *l_col;       // [N][KW] columns of L by column index (sampler)
+    const int32_t *pos_col;      // [pv*G] column of the variable at each position (-1: none)
     const int32_t *h_ptr;        // [M+1] rows of H (sampler)
     const int32_t *h_col;        // [E]
     const uint32_t *thr;         // [N] floor(p * 2^32) (sampler)
@@ -83,6 +87,17 @@ struct Variant {
     int block_threads;
     int min_blocks;      // launch bound: resident blocks per SM the register budget allows
 };
+
+// Placement of variables on positions and order of the edges inside each
+// check (the k of the check update), chosen for conflict-free shared-memory
+// access; optimize = false gives the identity placement and CSR order.
+struct Layout {
+    std::vector<int32_t> pos_of_var;   // [N]
+    std::vector<int32_t> var_at_pos;   // [npos], -1 where empty
+    std::vector<int32_t> edge_round;   // [nnz(H)] round k of each edge within its check
+};
+void plan_layout(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col, int G,
+                 int npos, int dc, bool optimize, Layout &out);
 
 int num_variants();
 const Variant &variant(int id);

@@ -104,12 +104,13 @@ struct Group {
 };
 
 // The cut of Algorithm 1 lines 4-7 for one shot: every row of D picks the
-// support variable of largest posterior LLR (windowed, hashed tie-break) and
-// sets its bit in cm (cm must be zero on entry).  load(slot0, col) returns
-// the posterior of a D entry.
-template <typename LoadL>
-__device__ __forceinline__ void cut_rows(const DevGraph &g, uint64_t gshot, int u, int G,
-                                         uint32_t *cm, LoadL load)
+// support variable of largest posterior LLR (windowed, hashed tie-break;
+// candidates in ascending column order) and marks it.  load(a, e) returns the
+// posterior of D entry a (e = its packed slot | position word); mark(a, e)
+// records the winner.
+template <typename LoadL, typename Mark>
+__device__ __forceinline__ void cut_rows(const DevGraph &g, uint64_t gshot, int u, int G, LoadL load,
+                                         Mark mark)
 {
     for (int r = u; r < g.Md; r += G) {
         const int b0 = __ldg(g.d_ptr + r), b1 = __ldg(g.d_ptr + r + 1);
@@ -117,26 +118,24 @@ __device__ __forceinline__ void cut_rows(const DevGraph &g, uint64_t gshot, int 
         float lmax = -f_inf();
         for (int a = b0; a < b1; ++a) {
             const uint32_t e = __ldg(g.d_ent + a);
-            lmax = fmaxf(lmax, load(e & 0xFFFFu, e >> 16));
+            lmax = fmaxf(lmax, load(a, e));
         }
         const float thr = isfinite(lmax) ? lmax - g.tie_rel * fmaxf(1.0f, fabsf(lmax)) : lmax;
         int nc = 0;
         for (int a = b0; a < b1; ++a) {
             const uint32_t e = __ldg(g.d_ent + a);
-            nc += load(e & 0xFFFFu, e >> 16) >= thr;
+            nc += load(a, e) >= thr;
         }
         if (nc == 0) continue;   // only with NaN posteriors
         const uint64_t h = splitmix64(g.tie_seed, gshot * (uint64_t)g.Md + (uint64_t)r);
         int pick = (int)(h % (uint64_t)nc);
-        uint32_t col = 0;
         for (int a = b0; a < b1; ++a) {
             const uint32_t e = __ldg(g.d_ent + a);
-            if (load(e & 0xFFFFu, e >> 16) >= thr) {
-                if (pick == 0) { col = e >> 16; break; }
+            if (load(a, e) >= thr) {
+                if (pick == 0) { mark(a, e); break; }
                 --pick;
             }
         }
-        atomicOr(cm + (col >> 5), 1u << (col & 31));
     }
 }
 
@@ -182,7 +181,8 @@ struct Lane {
 #pragma unroll
         for (int p = 0; p < PVM; ++p) {
             const int j = p * G + u;
-            lamv[p] = (p < g.pv && j < g.N) ? __ldg(g.lam + (size_t)p * G + u) : f_inf();
+            (void)j;
+            lamv[p] = p < g.pv ? __ldg(g.lam + (size_t)p * G + u) : f_inf();
         }
     }
 
@@ -208,9 +208,10 @@ struct Lane {
         for (int p = 0; p < PVM; ++p) {
             const int j = p * G + u;
             int deg = 0;
-            if (p < g.pv && j < g.N) {
+            (void)j;
+            if (p < g.pv) {
                 deg = __ldg(g.var_deg + (size_t)p * G + u);
-                vvalid |= 1u << p;
+                if (deg == 0xFF) deg = 0; else vvalid |= 1u << p;
             }
 #pragma unroll
             for (int m = 0; m < CVM; ++m) {
@@ -244,7 +245,7 @@ struct Decoder {
                 const uint32_t base = ln.lane_base + p * kPass;
 #pragma unroll
                 for (int m = 0; m < CVM; ++m) sts32(base + m * kSlot, (RV || ln.has(p, m)) ? v : 0u);
-                if (post_row && ((ln.vvalid >> p) & 1u)) post_row[p * G + u] = lam;
+                if (post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = lam;
             }
         }
         return hd & ln.vvalid;
@@ -327,7 +328,7 @@ struct Decoder {
                         if (m == 0 && last) q = Lp;
                         if (RV || ln.has(p, m)) sts32(base + m * kSlot, (__float_as_uint(q) & ~1u) | e);
                     }
-                    if (post_row && ((ln.vvalid >> p) & 1u)) post_row[p * G + u] = Lp;
+                    if (post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = Lp;
                 }
             }
             hd = nhd & ln.vvalid;
@@ -429,7 +430,8 @@ struct Decoder {
 #pragma unroll
                 for (int p = 0; p < PVM; ++p) {
                     const int j = p * G + u;
-                    if (p < g.pv && j < g.N && ((__ldg(ci + (j >> 5)) >> (j & 31)) & 1u)) {
+                    const int c = (p < g.pv && ((ln.vvalid >> p) & 1u)) ? __ldg(g.pos_col + j) : -1;
+                    if (c >= 0 && ((__ldg(ci + (c >> 5)) >> (c & 31)) & 1u)) {
                         ln.lamv[p] = f_inf();
                         lam_dirty = true;
                     }
@@ -440,7 +442,7 @@ struct Decoder {
                 if (post_row) {
 #pragma unroll
                     for (int p = 0; p < PVM; ++p)
-                        if (p < g.pv && ((ln.vvalid >> p) & 1u)) post_row[p * G + u] = ln.lamv[p];
+                        if (p < g.pv && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = ln.lamv[p];
                 }
             } else {
                 for (bool second = false;; second = true) {
@@ -455,9 +457,13 @@ struct Decoder {
                     ran_dc = true;
                     for (int x = u; x < g.cmw; x += G) cm[x] = 0;
                     grp.sync();
-                    cut_rows(g, gshot, u, G, cm, [&](uint32_t s0, uint32_t col) {
-                        return s0 == kNoEdge ? __ldg(g.lam + col) : slot[s0];
-                    });
+                    cut_rows(
+                        g, gshot, u, G,
+                        [&](int, uint32_t e) {
+                            const uint32_t s0 = e & 0xFFFFu;
+                            return s0 == kNoEdge ? __ldg(g.lam + (e >> 16)) : slot[s0];
+                        },
+                        [&](int, uint32_t e) { atomicOr(cm + ((e >> 16) >> 5), 1u << ((e >> 16) & 31)); });
                     grp.sync();
 #pragma unroll
                     for (int p = 0; p < PVM; ++p) {
@@ -496,7 +502,8 @@ struct Decoder {
                 for (int p = 0; p < PVM; ++p) {
                     if ((hd >> p) & 1u) {
                         const int j = p * G + u;
-                        atomicOr(cm + (j >> 5), 1u << (j & 31));
+                        const int c = __ldg(g.pos_col + j);
+                        atomicOr(cm + (c >> 5), 1u << (c & 31));
                         const uint32_t *lc = g.l_bits + (size_t)j * g.KW;
                         for (int x = 0; x < g.KW; ++x) {
                             const uint32_t v = __ldg(lc + x);
@@ -559,8 +566,13 @@ __global__ void cut_select_kernel(DevGraph g, int64_t B, const float *post, uint
         for (int x = threadIdx.x; x < g.NW; x += blockDim.x) cm[x] = 0;
         __syncthreads();
         const float *row = post + (size_t)b * g.N;
-        cut_rows(g, shot_offset + (uint64_t)b, threadIdx.x, blockDim.x, cm,
-                 [&](uint32_t, uint32_t col) { return __ldg(row + col); });
+        cut_rows(
+            g, shot_offset + (uint64_t)b, threadIdx.x, blockDim.x,
+            [&](int a, uint32_t) { return __ldg(row + __ldg(g.d_col + a)); },
+            [&](int a, uint32_t) {
+                const int c = __ldg(g.d_col + a);
+                atomicOr(cm + (c >> 5), 1u << (c & 31));
+            });
         __syncthreads();
         for (int x = threadIdx.x; x < g.NW; x += blockDim.x) cut_out[(size_t)b * g.NW + x] = cm[x];
         __syncthreads();
@@ -594,7 +606,7 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
         for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
             if ((eb[j >> 5] >> (j & 31)) & 1u) {
                 for (int x = 0; x < g.KW; ++x) {
-                    const uint32_t v = __ldg(g.l_bits + (size_t)j * g.KW + x);
+                    const uint32_t v = __ldg(g.l_col + (size_t)j * g.KW + x);
                     if (v) atomicXor(ob + x, v);
                 }
             }

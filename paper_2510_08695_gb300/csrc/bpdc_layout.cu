@@ -1,0 +1,219 @@
+// Host-side placement of Tanner-graph variables and ordering of check edges
+// for conflict-free shared-memory access.
+//
+// In the message layout every slot of the variable at position pos lies in
+// bank pos mod 32 (positions are p*G + u with G a multiple of 32).  The check
+// update of one warp handles 32 consecutive checks (a "group") and, in round k,
+// gathers and scatters the k-th edge of each: the round is conflict-free when
+// those 32 edges lie in 32 distinct banks.  Two choices are free and change no
+// arithmetic:
+//   1. which bank class each variable gets (its position mod 32): a local
+//      search (single moves under the per-bank capacity, then swaps) lowers,
+//      for every group, the number of edges a bank receives beyond the
+//      group's row weight;
+//   2. the order of the edges inside each check: per group, a proper edge
+//      colouring of the bipartite multigraph checks x banks with dc colours
+//      (Konig's theorem: bipartite multigraphs of maximum degree dc are
+//      dc-edge-colourable; built with alternating-path recolouring); a bank
+//      with more than dc edges in a group is split into virtual nodes of at
+//      most dc edges, whose copies then share rounds (unavoidable conflicts).
+#include <algorithm>
+#include <cstdint>
+#include <numeric>
+#include <vector>
+
+#include "bpdc_internal.h"
+
+namespace bpdc {
+namespace {
+
+// Deterministic xorshift for the local search order.
+struct Rng {
+    uint64_t s;
+    explicit Rng(uint64_t seed) : s(seed * 0x9E3779B97F4A7C15ull + 1) {}
+    uint32_t next()
+    {
+        s ^= s << 13;
+        s ^= s >> 7;
+        s ^= s << 17;
+        return (uint32_t)(s >> 16);
+    }
+};
+
+void assign_banks(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col,
+                  int cap, std::vector<int> &bank)
+{
+    const int ng = (M + 31) / 32;
+    std::vector<int> d(ng, 0);
+    for (int i = 0; i < M; ++i) d[i / 32] = std::max(d[i / 32], row_ptr[i + 1] - row_ptr[i]);
+    // groups touched by each variable, with multiplicity
+    std::vector<std::vector<int>> vg(N);
+    for (int i = 0; i < M; ++i)
+        for (int a = row_ptr[i]; a < row_ptr[i + 1]; ++a) vg[col[a]].push_back(i / 32);
+    bank.resize(N);
+    for (int j = 0; j < N; ++j) bank[j] = j % 32;
+    std::vector<int> n((size_t)ng * 32, 0);
+    for (int j = 0; j < N; ++j)
+        for (int g : vg[j]) n[(size_t)g * 32 + bank[j]]++;
+    std::vector<std::vector<int>> members(32);
+    for (int j = 0; j < N; ++j) members[bank[j]].push_back(j);
+    auto over = [&](int g, int x) { return std::max(0, x - d[g]); };
+    // cost change of moving j from b0 to b (n unchanged)
+    auto delta = [&](int j, int b0, int b) {
+        int dl = 0;
+        for (size_t t = 0; t < vg[j].size(); ++t) {
+            const int g = vg[j][t];
+            bool first = true;
+            for (size_t s = 0; s < t; ++s) first &= vg[j][s] != g;
+            if (!first) continue;
+            int c = 0;
+            for (int h : vg[j]) c += h == g;
+            const int x0 = n[(size_t)g * 32 + b0], x1 = n[(size_t)g * 32 + b];
+            dl += over(g, x0 - c) - over(g, x0) + over(g, x1 + c) - over(g, x1);
+        }
+        return dl;
+    };
+    auto move = [&](int j, int b0, int b) {
+        for (int g : vg[j]) {
+            n[(size_t)g * 32 + b0]--;
+            n[(size_t)g * 32 + b]++;
+        }
+        auto &m0 = members[b0];
+        m0.erase(std::find(m0.begin(), m0.end(), j));
+        members[b].push_back(j);
+        bank[j] = b;
+    };
+    Rng rng(2510);
+    std::vector<int> order(N);
+    std::iota(order.begin(), order.end(), 0);
+    for (int round = 0; round < 60; ++round) {
+        for (int k = N - 1; k > 0; --k) std::swap(order[k], order[rng.next() % (k + 1)]);
+        int improved = 0;
+        for (int j : order) {
+            const int b0 = bank[j];
+            int best = 0, bt = -1, jt = -1;
+            for (int b = 0; b < 32; ++b) {
+                if (b == b0) continue;
+                if ((int)members[b].size() < cap) {
+                    const int dl = delta(j, b0, b);
+                    if (dl < best) { best = dl; bt = b; jt = -1; }
+                } else {
+                    const auto &mb = members[b];
+                    for (int s = 0; s < 6 && !mb.empty(); ++s) {
+                        const int j2 = mb[rng.next() % mb.size()];
+                        const int d1 = delta(j, b0, b);
+                        move(j, b0, b);
+                        const int d2 = delta(j2, b, b0);
+                        move(j, b, b0);
+                        if (d1 + d2 < best) { best = d1 + d2; bt = b; jt = j2; }
+                    }
+                }
+            }
+            if (bt >= 0) {
+                move(j, b0, bt);
+                if (jt >= 0) move(jt, bt, b0);
+                ++improved;
+            }
+        }
+        if (!improved) break;
+    }
+}
+
+// Konig colouring of one group's bipartite multigraph; left = checks (local
+// index), right = virtual banks.  edges: (left, right); returns colour per edge.
+std::vector<int> color_group(int nl, int nr, int D, const std::vector<std::pair<int, int>> &edges)
+{
+    const int E = (int)edges.size();
+    std::vector<int> atL((size_t)nl * D, -1), atR((size_t)nr * D, -1), colr(E, -1);
+    for (int e = 0; e < E; ++e) {
+        const int l = edges[e].first, r = edges[e].second;
+        int a = -1, b = -1;
+        for (int c = 0; c < D && a < 0; ++c)
+            if (atL[(size_t)l * D + c] < 0) a = c;
+        for (int c = 0; c < D && b < 0; ++c)
+            if (atR[(size_t)r * D + c] < 0) b = c;
+        if (a < 0 || b < 0) continue;   // cannot happen when degrees are <= D
+        if (atR[(size_t)r * D + a] >= 0) {
+            // flip the a/b alternating path that starts at r with colour a
+            std::vector<int> path;
+            int node = r;
+            bool right = true;
+            int c = a;
+            while (true) {
+                const int f = right ? atR[(size_t)node * D + c] : atL[(size_t)node * D + c];
+                if (f < 0) break;
+                path.push_back(f);
+                node = right ? edges[f].first : edges[f].second;
+                right = !right;
+                c = (c == a) ? b : a;
+            }
+            for (int f : path) {
+                atL[(size_t)edges[f].first * D + colr[f]] = -1;
+                atR[(size_t)edges[f].second * D + colr[f]] = -1;
+            }
+            for (int f : path) {
+                colr[f] = (colr[f] == a) ? b : a;
+                atL[(size_t)edges[f].first * D + colr[f]] = f;
+                atR[(size_t)edges[f].second * D + colr[f]] = f;
+            }
+        }
+        colr[e] = a;
+        atL[(size_t)l * D + a] = e;
+        atR[(size_t)r * D + a] = e;
+    }
+    return colr;
+}
+
+}  // namespace
+
+void plan_layout(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col, int G,
+                 int npos, int dc, bool optimize, Layout &out)
+{
+    out.pos_of_var.assign(N, -1);
+    out.var_at_pos.assign(npos, -1);
+    out.edge_round.assign(col.size(), 0);
+    if (!optimize || G % 32 != 0) {
+        for (int j = 0; j < N; ++j) {
+            out.pos_of_var[j] = j;
+            out.var_at_pos[j] = j;
+        }
+        for (int i = 0; i < M; ++i)
+            for (int a = row_ptr[i], k = 0; a < row_ptr[i + 1]; ++a, ++k) out.edge_round[a] = k;
+        return;
+    }
+    // 1. bank classes
+    std::vector<int> bank;
+    assign_banks(M, N, row_ptr, col, npos / 32, bank);
+    std::vector<int> next(32, 0);   // k-th free position of a bank: k*32 + b
+    for (int j = 0; j < N; ++j) {
+        const int b = bank[j];
+        const int pos = next[b]++ * 32 + b;
+        out.pos_of_var[j] = pos;
+        out.var_at_pos[pos] = j;
+    }
+    // 2. edge rounds per group of 32 checks
+    for (int g0 = 0; g0 < M; g0 += 32) {
+        const int g1 = std::min(M, g0 + 32);
+        std::vector<std::pair<int, int>> edges;
+        std::vector<int> eid;
+        int per_bank[32] = {0};
+        std::vector<int> vnode;
+        for (int i = g0; i < g1; ++i)
+            for (int a = row_ptr[i]; a < row_ptr[i + 1]; ++a) {
+                const int b = out.pos_of_var[col[a]] % 32;
+                const int virt = per_bank[b]++ / dc;   // split overloaded banks
+                edges.emplace_back(i - g0, b * 64 + virt);
+                eid.push_back(a);
+            }
+        // compact right-node ids
+        std::vector<int> ids;
+        for (auto &e : edges) ids.push_back(e.second);
+        std::sort(ids.begin(), ids.end());
+        ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+        for (auto &e : edges) e.second = (int)(std::lower_bound(ids.begin(), ids.end(), e.second) - ids.begin());
+        const std::vector<int> c = color_group(g1 - g0, (int)ids.size(), dc, edges);
+        for (size_t t = 0; t < edges.size(); ++t) out.edge_round[eid[t]] = c[t];
+    }
+}
+
+}  // namespace bpdc

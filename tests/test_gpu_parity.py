@@ -197,6 +197,22 @@ def test_plain_and_persistent_identical_and_offsets(pkg):
         assert (a[k] == torch.cat([c1[k], c2[k]])).all(), k
 
 
+@pytest.mark.parametrize("name", ["bb144", "hgp", "phen"])
+def test_layouts_give_identical_results(pkg, name):
+    """The bank-conflict-aware layout changes no arithmetic: bit-identical outputs."""
+    P = {"bb144": lambda: bi.bb_problem("bb144", 0.07), "hgp": lambda: bi.hgp_problem(0.06),
+         "phen": lambda: bi.phenomenological_bb_problem("bb144", 12, 0.008)}[name]()
+    _, s, o = sample_shots(P, SEED + 21, 0, 1500 if P.N < 1000 else 400)
+    g = pkg.Graph.from_problem(P)
+    outs = []
+    for mode in (1, 0):
+        g.set_layout(mode)
+        outs.append(g.decode(to_dev(s), 0, obs_true=to_dev(o), posterior=True))
+    for k in ("corrections", "status", "logical_flips", "iterations", "posterior_llr"):
+        a, b = outs[0][k], outs[1][k]
+        assert (a == b).all() or (k == "posterior_llr" and bool(((a == b) | (a.isnan() & b.isnan())).all())), k
+
+
 def test_decode_multi_equals_single(pkg):
     import torch
     probs = [bi.bb_problem("bb72", 0.04), bi.bb_problem("bb144", 0.05), bi.hgp_problem(0.05),

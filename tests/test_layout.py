@@ -1,0 +1,48 @@
+"""The message-layout planner (host only): variable positions are a valid
+placement, edge rounds are a valid per-check order, and the planned layout
+cuts the modelled shared-memory wavefronts of the check update."""
+import numpy as np
+import pytest
+
+import bpdc_inputs as bi
+from paper_2510_08695_gb300 import _bpdc
+
+
+def wavefronts(H, pos, rnd):
+    """Sum over groups of 32 checks and rounds of the largest bank multiplicity."""
+    H = H.tocsr()
+    M = H.shape[0]
+    total = ideal = 0
+    for g0 in range(0, M, 32):
+        rows = range(g0, min(M, g0 + 32))
+        d = max(H.indptr[i + 1] - H.indptr[i] for i in rows)
+        ideal += d
+        for k in range(d):
+            banks = [pos[H.indices[a]] % 32 for i in rows for a in range(H.indptr[i], H.indptr[i + 1])
+                     if rnd[a] == k]
+            total += np.bincount(banks, minlength=32).max() if banks else 0
+    return total, ideal
+
+
+@pytest.mark.parametrize("name,G", [("bb72", 32), ("bb144", 32), ("hgp", 256), ("phen", 256)])
+def test_layout_is_valid_and_cuts_conflicts(name, G):
+    P = {"bb72": lambda: bi.bb_problem("bb72", 0.05), "bb144": lambda: bi.bb_problem("bb144", 0.05),
+         "hgp": lambda: bi.hgp_problem(0.05),
+         "phen": lambda: bi.phenomenological_bb_problem("bb144", 12, 0.01)}[name]()
+    H = P.H.tocsr()
+    N = H.shape[1]
+    npos = -(-N // G) * G
+    pos, rnd = _bpdc.layout_plan(H, G, True)
+    # positions: injective, in range, no bank above its capacity
+    assert len(set(pos.tolist())) == N and pos.min() >= 0 and pos.max() < npos
+    assert np.bincount(pos % 32, minlength=32).max() <= npos // 32
+    # rounds: distinct within each check and below the row weight
+    dmax = int(np.diff(H.indptr).max())
+    for i in range(H.shape[0]):
+        r = rnd[H.indptr[i]:H.indptr[i + 1]]
+        assert len(set(r.tolist())) == len(r) and r.max() < dmax
+    pos0, rnd0 = _bpdc.layout_plan(H, G, False)
+    assert (pos0 == np.arange(N)).all()
+    w_opt, ideal = wavefronts(H, pos, rnd)
+    w_nat, _ = wavefronts(H, pos0, rnd0)
+    assert w_opt < 0.8 * w_nat and w_opt <= 1.5 * ideal, (w_opt, w_nat, ideal)
