@@ -271,7 +271,6 @@ struct Decoder {
                     const bool live = (ln.cvalid >> p) & 1u;
                     uint32_t qb[DCM];
                     float mn1 = f_inf(), mn2 = f_inf();
-                    int kmin = 0;
                     uint32_t S = ((sbits >> p) & 1u) ? 0x80000001u : 0u;
 #pragma unroll
                     for (int k = 0; k < DCM; ++k) {
@@ -280,19 +279,22 @@ struct Decoder {
                         qb[k] = b;
                         S ^= b;   // bit 31: sign parity, bit 0: hard-decision parity
                         const float av = fabsf(__uint_as_float(b));
-                        kmin = av < mn1 ? k : kmin;
                         mn2 = fminf(mn2, fmaxf(mn1, av));
                         mn1 = fminf(mn1, av);
                     }
                     unsat |= S;
                     if (scatter) {
+                        // the minimum over the other edges is min2 for the edge
+                        // holding min1 and min1 for all others; with a tie at
+                        // min1 both are equal, so no argmin is needed
                         const uint32_t Sm = S & 0x80000000u;
                         const uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap)) ^ Sm;
                         const uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap)) ^ Sm;
 #pragma unroll
                         for (int k = 0; k < DCM; ++k) {
                             const uint32_t a = ln.addr[p * DCM + k];
-                            const uint32_t out = ((k == kmin) ? m2 : m1) ^ (qb[k] & 0x80000000u);
+                            const bool is_min = fabsf(__uint_as_float(qb[k])) == mn1;
+                            const uint32_t out = (is_min ? m2 : m1) ^ (qb[k] & 0x80000000u);
                             if (RC ? live : (a != ln.inf_addr)) sts32(a, out);
                         }
                     }
@@ -324,10 +326,11 @@ struct Decoder {
                     nhd |= e << p;
 #pragma unroll
                     for (int m = 0; m < CVM; ++m) {
-                        float q = (m == CVM - 1) ? pre[m] : pre[m] + suf[m + 1];
-                        if (m == 0 && last) q = Lp;
+                        const float q = (m == CVM - 1) ? pre[m] : pre[m] + suf[m + 1];
                         if (RV || ln.has(p, m)) sts32(base + m * kSlot, (__float_as_uint(q) & ~1u) | e);
                     }
+                    if (last && (RV || ln.has(p, 0)))   // slot 0 keeps L for the cut selection
+                        sts32(base, (__float_as_uint(Lp) & ~1u) | e);
                     if (post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = Lp;
                 }
             }
