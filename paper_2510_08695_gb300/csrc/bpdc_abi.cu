@@ -162,7 +162,7 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     }
     if (P.pc > v.pc_max || P.pv > v.pv_max || dmax > v.dc_max || cmax > v.cv_max) return false;
     if (v.regular_rows && (dmin != v.dc_max || dmax != v.dc_max)) return false;
-    if (v.regular_cols && (cmin != v.cv_max || cmax != v.cv_max)) return false;
+    if (cmin < v.cv_min) return false;
     P.dc = std::max(dmax, 1);
     P.cv = v.cv_max;
     const long slots = (long)P.pv * P.cv * G;

@@ -82,7 +82,7 @@ struct Variant {
     int id;
     int G;
     int pc_max, dc_max, pv_max, cv_max;
-    bool regular_cols;   // every variable has exactly cv_max edges
+    int cv_min;          // every variable has at least cv_min edges
     bool regular_rows;   // every check has exactly dc_max edges
     int block_threads;
     int min_blocks;      // launch bound: resident blocks per SM the register budget allows

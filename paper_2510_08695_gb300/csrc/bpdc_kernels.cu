@@ -155,10 +155,21 @@ __device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v));
 }
 
+// Store under a predicate evaluated inside the PTX, so that the compiler
+// emits one predicated store instead of a branch around the inline asm.
+__device__ __forceinline__ void sts32_if(uint32_t a, uint32_t v, bool pred)
+{
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.u32 q, %2, 0;\n\t"
+        "@q st.shared.b32 [%0], %1;\n\t}" ::"r"(a), "r"(v), "r"((uint32_t)pred));
+}
+
 // Per-lane state that depends only on the graph (reloaded when a launch
-// switches to a batch of another graph).  RV: every variable has exactly CVM
-// edges; RC: every check has exactly DCM edges.
-template <int G, int PCM, int DCM, int PVM, int CVM, bool RV, bool RC>
+// switches to a batch of another graph).  CMIN: every variable has at least
+// CMIN edges (slots below CMIN need no store predicate); RC: every check has
+// exactly DCM edges.
+template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC>
 struct Lane {
     static constexpr int kVmWords = (PVM * CVM + 31) / 32;
 
@@ -223,9 +234,9 @@ struct Lane {
     }
 };
 
-template <int G, int PCM, int DCM, int PVM, int CVM, bool RV, bool RC>
+template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC>
 struct Decoder {
-    using L = Lane<G, PCM, DCM, PVM, CVM, RV, RC>;
+    using L = Lane<G, PCM, DCM, PVM, CVM, CMIN, RC>;
     static constexpr uint32_t kPass = 4u * CVM * G;   // bytes between variable passes
     static constexpr uint32_t kSlot = 4u * G;         // bytes between a variable's slots
 
@@ -244,7 +255,7 @@ struct Decoder {
                 const uint32_t v = (__float_as_uint(lam) & ~1u) | e;
                 const uint32_t base = ln.lane_base + p * kPass;
 #pragma unroll
-                for (int m = 0; m < CVM; ++m) sts32(base + m * kSlot, (RV || ln.has(p, m)) ? v : 0u);
+                for (int m = 0; m < CVM; ++m) sts32(base + m * kSlot, (m < CMIN || ln.has(p, m)) ? v : 0u);
                 if (post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = lam;
             }
         }
@@ -288,14 +299,16 @@ struct Decoder {
                         // holding min1 and min1 for all others; with a tie at
                         // min1 both are equal, so no argmin is needed
                         const uint32_t Sm = S & 0x80000000u;
-                        const uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap)) ^ Sm;
-                        const uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap)) ^ Sm;
+                        uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap)) ^ Sm;
+                        uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap)) ^ Sm;
+                        if (RC && !live) m1 = m2 = 0x7F800000u;   // idle check: writes +inf back
 #pragma unroll
                         for (int k = 0; k < DCM; ++k) {
                             const uint32_t a = ln.addr[p * DCM + k];
                             const bool is_min = fabsf(__uint_as_float(qb[k])) == mn1;
                             const uint32_t out = (is_min ? m2 : m1) ^ (qb[k] & 0x80000000u);
-                            if (RC ? live : (a != ln.inf_addr)) sts32(a, out);
+                            if (RC) sts32(a, out);
+                            else sts32_if(a, out, a != ln.inf_addr);
                         }
                     }
                 }
@@ -327,10 +340,15 @@ struct Decoder {
 #pragma unroll
                     for (int m = 0; m < CVM; ++m) {
                         const float q = (m == CVM - 1) ? pre[m] : pre[m] + suf[m + 1];
-                        if (RV || ln.has(p, m)) sts32(base + m * kSlot, (__float_as_uint(q) & ~1u) | e);
+                        const uint32_t qv = (__float_as_uint(q) & ~1u) | e;
+                        if (m < CMIN) sts32(base + m * kSlot, qv);
+                        else sts32_if(base + m * kSlot, qv, ln.has(p, m));
                     }
-                    if (last && (RV || ln.has(p, 0)))   // slot 0 keeps L for the cut selection
-                        sts32(base, (__float_as_uint(Lp) & ~1u) | e);
+                    if (last) {   // slot 0 keeps L for the cut selection
+                        const uint32_t lv = (__float_as_uint(Lp) & ~1u) | e;
+                        if (CMIN > 0) sts32(base, lv);
+                        else sts32_if(base, lv, ln.has(p, 0));
+                    }
                     if (post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = Lp;
                 }
             }
@@ -537,7 +555,7 @@ struct Decoder {
     }
 };
 
-template <int G, int PCM, int DCM, int PVM, int CVM, bool RV, bool RC, int BLOCK, int MINB>
+template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int region_words)
 {
     extern __shared__ uint32_t smem[];
@@ -556,7 +574,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int 
         grp.leader = 0;
     }
     uint32_t *region = smem + (size_t)gib * region_words;
-    Decoder<G, PCM, DCM, PVM, CVM, RV, RC>::decode(ld, region, grp, gib);
+    Decoder<G, PCM, DCM, PVM, CVM, CMIN, RC>::decode(ld, region, grp, gib);
 }
 
 // Cut selection alone, one block per shot (same selection code as the fused kernel).
@@ -631,21 +649,23 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
 // variable, block threads).
 // (id, G, check passes, row weight, variable passes, column weight, regular
 // columns, regular rows, block threads, min blocks per SM)
-#define BPDC_VARIANTS(X)                                 \
-    X(0, 32, 3, 6, 5, 3, true, true, 256, 4)             \
-    X(1, 256, 5, 7, 10, 4, false, true, 256, 3)          \
-    X(2, 512, 3, 7, 5, 4, false, true, 512, 2)           \
-    X(3, 256, 4, 8, 11, 3, false, false, 256, 3)         \
-    X(4, 512, 2, 8, 6, 3, false, false, 512, 2)          \
-    X(5, 32, 4, 8, 8, 4, false, false, 256, 4)           \
-    X(6, 128, 10, 7, 20, 4, false, true, 128, 6)         \
-    X(7, 32, 3, 6, 5, 3, true, true, 256, 3)             \
-    X(8, 256, 5, 7, 10, 4, false, true, 256, 2)          \
-    X(9, 512, 3, 7, 5, 4, false, true, 512, 1)           \
-    X(10, 256, 4, 8, 11, 3, false, false, 256, 2)
+// (id, G, check passes, row weight, variable passes, column weight, minimum
+// column weight, regular rows, block threads, min blocks per SM)
+#define BPDC_VARIANTS(X)                            \
+    X(0, 32, 3, 6, 5, 3, 3, true, 256, 4)           \
+    X(1, 256, 5, 7, 10, 4, 3, true, 256, 3)         \
+    X(2, 512, 3, 7, 5, 4, 3, true, 512, 2)          \
+    X(3, 256, 4, 8, 11, 3, 2, false, 256, 3)        \
+    X(4, 512, 2, 8, 6, 3, 2, false, 512, 2)         \
+    X(5, 32, 4, 8, 8, 4, 1, false, 256, 4)          \
+    X(6, 128, 10, 7, 20, 4, 3, true, 128, 6)        \
+    X(7, 32, 3, 6, 5, 3, 3, true, 256, 3)           \
+    X(8, 256, 5, 7, 10, 4, 3, true, 256, 2)         \
+    X(9, 512, 3, 7, 5, 4, 3, true, 512, 1)          \
+    X(10, 256, 4, 8, 11, 3, 2, false, 256, 2)
 
 static const Variant kVariants[] = {
-#define X(id, G, PC, DC, PV, CV, RV, RC, BLK, MB) {id, G, PC, DC, PV, CV, RV, RC, BLK, MB},
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, BLK, MB) {id, G, PC, DC, PV, CV, CMIN, RC, BLK, MB},
     BPDC_VARIANTS(X)
 #undef X
 };
@@ -656,8 +676,8 @@ const Variant &variant(int id) { return kVariants[id]; }
 static const void *variant_fn(int id)
 {
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, RV, RC, BLK, MB) \
-    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, RV, RC, BLK, MB>;
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, BLK, MB) \
+    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, CMIN, RC, BLK, MB>;
         BPDC_VARIANTS(X)
 #undef X
     default: return nullptr;
@@ -706,9 +726,9 @@ cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_byte
 {
     const int region = smem_bytes / 4 / (kVariants[id].block_threads / kVariants[id].G);
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, RV, RC, BLK, MB)                                                     \
-    case id:                                                                                          \
-        decode_kernel<G, PC, DC, PV, CV, RV, RC, BLK, MB><<<grid, BLK, smem_bytes, s>>>(ld, region); \
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, BLK, MB)                                                     \
+    case id:                                                                                            \
+        decode_kernel<G, PC, DC, PV, CV, CMIN, RC, BLK, MB><<<grid, BLK, smem_bytes, s>>>(ld, region); \
         return cudaGetLastError();
         BPDC_VARIANTS(X)
 #undef X
