@@ -396,27 +396,34 @@ def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
     e2e = len(batches) * args.shots_per_point * args.steps / (t0.elapsed_time(t1) / 1e3)
     line["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # ---- request latency: seeded trace of BB72 / BB144 requests of 1..1024 shots
-    rng = np.random.default_rng(7)
-    small = [b for b in batches if b["code"] in ("bb72", "bb144") and b["p"] in (0.01, 0.05)]
-    lat = {"persistent": [], "plain": []}
-    for mode in ("plain", "persistent"):
-        per_shot = []
-        for r in range(400):
-            b = small[int(rng.integers(len(small)))]
-            n = int(rng.integers(1, 1025))
-            s0 = int(rng.integers(0, args.shots_per_point - n))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            b["graph"].decode(b["syndromes"][s0:s0 + n], b["shot_offset"] + s0, persistent=(mode == "persistent"))
-            e1.record(stream)
-            e1.synchronize()
-            per_shot.append(e0.elapsed_time(e1) * 1e3)
-        lat[mode] = per_shot
-    line["latency_us"] = {m: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
-                          for m, v in lat.items()}
-    line["p99_us_per_shot"] = line["latency_us"]["persistent"]["p99"]
+    # ---- serving: seeded Poisson trace of BB72 / BB144 requests of 1..1024 shots
+    from paper_2510_08695_gb300 import serving
+    small = [b for b in batches if b["code"] in ("bb72", "bb144") and b["p"] == 0.05]
+    graphs = [b["graph"] for b in small]
+    pools = [b["syndromes"][:200000].cpu().pin_memory() for b in small]
+    calib = serving.poisson_trace(300, rate_per_s=1e9, n_graphs=len(graphs), seed=11)
+    cal = serving.replay(serving.PlainDecoder(graphs), calib, pools)
+    service_s = (max(r.done for r in cal) - min(r.arrival for r in cal)) / len(cal)
+    rate = 0.7 / service_s
+    trace = serving.poisson_trace(4000, rate_per_s=rate, n_graphs=len(graphs), seed=12)
+    lat = {}
+    served = {}
+    for name, eng in (("plain", serving.PlainDecoder(graphs)), ("server", serving.Server(graphs, slots=4))):
+        reqs = serving.replay(eng, trace, pools)
+        l_us = np.array([(r.done - r.arrival) * 1e6 for r in reqs])
+        shots = sum(r.syndromes.shape[0] for r in reqs)
+        span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+        lat[name] = {"p50_us": float(np.percentile(l_us, 50)), "p99_us": float(np.percentile(l_us, 99)),
+                     "shots_per_s": shots / span}
+        served[name] = reqs
+    same = all(torch.equal(a.result[k], b.result[k]) for a, b in zip(served["plain"], served["server"])
+               for k in ("corrections", "status", "logical_flips"))
+    line["serving"] = {"trace": f"{len(trace)} Poisson requests of 1..1024 shots over BB[[72,12,6]] and "
+                                f"BB[[144,12,12]] at p=0.05, {rate:.0f} requests/s (70% of the plain decoder's "
+                                "capacity); latency = arrival to results on the host",
+                       "plain_per_request_kernel": lat["plain"], "continuous_batching_server": lat["server"],
+                       "server_slots": 4, "identical_results": same}
+    line["p99_us_per_shot"] = lat["server"]["p99_us"]
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample of the workload
     import oracle

@@ -175,7 +175,9 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     int region = 12 + P.slots + P.cmw + std::max(P.KW, 1);   // 12 misc words (see the kernels)
     region = (region + 3) & ~3;
     P.region = region;
-    if ((long)(v.block_threads / G) * region * 4 > kMaxSmemPerBlock) return false;
+    // shared addresses are kept as 16-bit values in the kernels: the block's
+    // dynamic shared memory plus the reserved 1 KB must stay below 64 KB
+    if ((long)(v.block_threads / G) * region * 4 + 1024 > 65535) return false;
     // variable placement and edge order (bpdc_layout.cu)
     const int npos = P.pv * G;
     Layout lay;

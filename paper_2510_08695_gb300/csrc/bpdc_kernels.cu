@@ -173,7 +173,10 @@ template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC>
 struct Lane {
     static constexpr int kVmWords = (PVM * CVM + 31) / 32;
 
-    uint32_t addr[PCM * DCM];  // shared byte address of each check edge's slot (the +inf word if none)
+    static constexpr int kAddrWords = (PCM * DCM + 1) / 2;
+    // shared byte address of each check edge's slot (the +inf word if none),
+    // two 16-bit addresses per word (blocks use less than 64 KB of shared memory)
+    uint32_t aw[kAddrWords];
     uint32_t vm[kVmWords];     // bit (p*CVM + m): the variable at pass p has an m-th edge
     uint32_t vvalid;           // bit p: a variable sits at pass p
     uint32_t cvalid;           // bit p: a check sits at pass p
@@ -185,6 +188,12 @@ struct Lane {
     {
         const int n = p * CVM + m;
         return (vm[n >> 5] >> (n & 31)) & 1u;
+    }
+
+    __device__ __forceinline__ uint32_t addr(int p, int k) const
+    {
+        const int n = p * DCM + k;
+        return (n & 1) ? (aw[n >> 1] >> 16) : (aw[n >> 1] & 0xFFFFu);
     }
 
     __device__ void reload_lam(const DevGraph &g, int u)
@@ -203,13 +212,17 @@ struct Lane {
         inf_addr = inf_word;
         cvalid = 0;
 #pragma unroll
+        for (int w = 0; w < kAddrWords; ++w) aw[w] = 0;
+#pragma unroll
         for (int p = 0; p < PCM; ++p) {
             if (p < g.pc && p * G + u < g.M) cvalid |= 1u << p;
 #pragma unroll
             for (int k = 0; k < DCM; ++k) {
                 uint32_t v = kNoEdge;
                 if (p < g.pc && k < g.dc) v = __ldg(g.chk_idx + ((size_t)p * g.dc + k) * G + u);
-                addr[p * DCM + k] = (v == kNoEdge) ? inf_word : slot_base + 4u * v;
+                const uint32_t a = ((v == kNoEdge) ? inf_word : slot_base + 4u * v) & 0xFFFFu;
+                const int n = p * DCM + k;
+                aw[n >> 1] |= a << ((n & 1) * 16);
             }
         }
 #pragma unroll
@@ -286,7 +299,7 @@ struct Decoder {
 #pragma unroll
                     for (int k = 0; k < DCM; ++k) {
                         // unused slots point at the group's +inf word
-                        const uint32_t b = lds32(ln.addr[p * DCM + k]);
+                        const uint32_t b = lds32(ln.addr(p, k));
                         qb[k] = b;
                         S ^= b;   // bit 31: sign parity, bit 0: hard-decision parity
                         const float av = fabsf(__uint_as_float(b));
@@ -304,7 +317,7 @@ struct Decoder {
                         if (RC && !live) m1 = m2 = 0x7F800000u;   // idle check: writes +inf back
 #pragma unroll
                         for (int k = 0; k < DCM; ++k) {
-                            const uint32_t a = ln.addr[p * DCM + k];
+                            const uint32_t a = ln.addr(p, k);
                             const bool is_min = fabsf(__uint_as_float(qb[k])) == mn1;
                             const uint32_t out = (is_min ? m2 : m1) ^ (qb[k] & 0x80000000u);
                             if (RC) sts32(a, out);
