@@ -31,6 +31,19 @@ def bb_problem(name: str, p: float) -> Problem:
     return codes.code_capacity_problem(hx, hz, p, f"{name}_p{p:g}", oz=oz)
 
 
+@functools.lru_cache(maxsize=None)
+def _surface(d):
+    hx, hz = codes.rotated_surface_code(d)
+    oz = codes.logical_basis(hx, hz)
+    return hx, hz, oz
+
+
+def surface_problem(d: int, p: float) -> Problem:
+    """Code-capacity problem for the rotated surface code [[d^2, 1, d]]."""
+    hx, hz, oz = _surface(d)
+    return codes.code_capacity_problem(hx, hz, p, f"surface{d}_p{p:g}", oz=oz)
+
+
 def hgp_problem(p: float, n: int = 40, seed: int = 2510) -> Problem:
     """Code-capacity problem for the hypergraph product of a seeded (3,4)-regular code."""
     _, hx, hz, oz = _hgp(n, seed)

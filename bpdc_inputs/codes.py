@@ -124,6 +124,44 @@ def bb_code(name: str):
 
 
 # ----------------------------------------------------------------------------
+# Rotated surface code (Sec. II.B.1)
+# ----------------------------------------------------------------------------
+
+def rotated_surface_code(d: int):
+    """(H_X, H_Z) of the rotated surface code [[d^2, 1, d]], d odd.
+
+    Data qubit (r, c), r, c in [0, d), has index r*d + c.  Plaquette (i, j),
+    i, j in [-1, d-1], covers the qubits (i, j), (i+1, j), (i, j+1), (i+1, j+1)
+    that exist; plaquettes with i + j even are Z-type, odd X-type.  Interior
+    plaquettes (i, j in [0, d-2]) are all kept; on the boundary only weight-2
+    X plaquettes on the top and bottom rows (i = -1, d-1) and weight-2 Z
+    plaquettes on the left and right columns (j = -1, d-1) are kept.  Every
+    stabilizer has weight <= 4 and every qubit is in <= 2 stabilizers of each
+    type.
+    """
+    assert d % 2 == 1 and d >= 3
+    hx, hz = [], []
+    for i in range(-1, d):
+        for j in range(-1, d):
+            qs = [r * d + c for r in (i, i + 1) for c in (j, j + 1) if 0 <= r < d and 0 <= c < d]
+            interior = 0 <= i <= d - 2 and 0 <= j <= d - 2
+            ztype = (i + j) % 2 == 0
+            if interior:
+                (hz if ztype else hx).append(qs)
+            elif len(qs) == 2:
+                if not ztype and i in (-1, d - 1) and 0 <= j <= d - 2:
+                    hx.append(qs)
+                if ztype and j in (-1, d - 1) and 0 <= i <= d - 2:
+                    hz.append(qs)
+    def mat(rows):
+        m = np.zeros((len(rows), d * d), dtype=np.uint8)
+        for r, qs in enumerate(rows):
+            m[r, qs] = 1
+        return m
+    return mat(hx), mat(hz)
+
+
+# ----------------------------------------------------------------------------
 # Hypergraph-product code of a seeded (3,4)-regular classical code
 # ----------------------------------------------------------------------------
 

@@ -11,8 +11,8 @@
  *               acts on (Algorithm 1, Sec. III.A; Sec. IV.B);
  *   p  (N)      prior error probabilities (Eq. 8).
  *
- * The decoder runs flooding normalized min-sum BP (Sec. II.C.1) with FP32
- * messages.  When BP does not reproduce the syndrome within T_iter
+ * The decoder runs flooding BP (Sec. II.C.1) with FP32 messages and the
+ * normalized min-sum or the product-sum check rule.  When BP does not reproduce the syndrome within T_iter
  * iterations it cuts, for every row of D, the support variable with the
  * highest posterior LLR (lowest error probability), and runs BP once more on
  * the cut graph with the original priors (Algorithm 1 with the Sec. III.B
@@ -69,8 +69,9 @@ typedef struct {
 
 /* Decoding options, fixed when the graph is created. */
 typedef struct {
-    int32_t variant;   /* 0: normalized min-sum (the only one implemented) */
-    float ms_scale;    /* alpha, the min-sum scale factor, in (0, 1] */
+    int32_t variant;   /* check rule: 0 normalized min-sum, 1 product-sum (Sec. II.C.1
+                          cites both; the paper uses product-sum for surface codes) */
+    float ms_scale;    /* alpha, the min-sum scale factor, in (0, 1] (unused by product-sum) */
     int32_t max_iter;  /* T_iter, the BP iteration limit of each run, 0..65535 */
     int32_t dc_enable; /* 1: degeneracy cutting on BP failure; 0: plain BP */
     int32_t dc_prior;  /* 0: second BP on the priors p (Sec. III.B, BB codes);

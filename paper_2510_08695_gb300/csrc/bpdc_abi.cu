@@ -160,6 +160,7 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
         cmax = std::max(cmax, deg[j]);
         cmin = std::min(cmin, deg[j]);
     }
+    if (v.rule != g.opts.variant) return false;
     if (P.pc > v.pc_max || P.pv > v.pv_max || dmax > v.dc_max || cmax > v.cv_max) return false;
     if (v.regular_rows && (dmin != v.dc_max || dmax != v.dc_max)) return false;
     if (cmin < v.cv_min) return false;
@@ -250,7 +251,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
 {
     // automatic preference: one warp per shot for small graphs, then the
     // 256- and 512-thread groups
-    static const int kOrder[] = {0, 5, 1, 3, 2, 4, 6};
+    static const int kOrder[] = {0, 12, 5, 11, 1, 3, 2, 4, 6};
     Packed P{};
     int vid = -1;
     for (int id : kOrder) {
@@ -456,7 +457,8 @@ int bpdc_graph_create(const bpdc_csr *H, const bpdc_csr *L, const bpdc_csr *D, c
     if (!priors) return fail(BPDC_ERR_INVALID_ARG, "priors is NULL");
     bpdc_opts o;
     if (opts) o = *opts; else bpdc_opts_default(&o);
-    if (o.variant != 0) return fail(BPDC_ERR_UNSUPPORTED, "only the min-sum variant (0) is implemented");
+    if (o.variant != 0 && o.variant != 1)
+        return fail(BPDC_ERR_INVALID_ARG, "variant must be 0 (min-sum) or 1 (product-sum)");
     if (!(o.ms_scale > 0.0f && o.ms_scale <= 1.0f)) return fail(BPDC_ERR_INVALID_ARG, "ms_scale must be in (0, 1]");
     if (o.max_iter < 0 || o.max_iter > 65535) return fail(BPDC_ERR_INVALID_ARG, "max_iter must be in [0, 65535]");
     if ((o.dc_enable != 0 && o.dc_enable != 1) || (o.dc_prior != 0 && o.dc_prior != 1))

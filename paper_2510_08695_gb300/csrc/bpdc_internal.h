@@ -84,6 +84,7 @@ struct Variant {
     int pc_max, dc_max, pv_max, cv_max;
     int cv_min;          // every variable has at least cv_min edges
     bool regular_rows;   // every check has exactly dc_max edges
+    int rule;            // check rule: 0 normalized min-sum, 1 product-sum
     int block_threads;
     int min_blocks;      // launch bound: resident blocks per SM the register budget allows
 };

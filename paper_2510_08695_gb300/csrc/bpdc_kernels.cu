@@ -139,6 +139,12 @@ __device__ __forceinline__ void cut_rows(const DevGraph &g, uint64_t gshot, int 
     }
 }
 
+// phi(x) = -log(tanh(x / 2)) for x >= 0 (phi(0) = +inf, phi(+inf) = 0); phi is
+// its own inverse and 2 atanh(prod tanh(x_j / 2)) = phi(sum phi(x_j)), the
+// product-sum check rule (Sec. II.C.1 cites it) in a form that keeps FP32
+// accurate: expm1 and log1p avoid the cancellations of tanh near 1.
+__device__ __forceinline__ float phi(float x) { return log1pf(2.0f / expm1f(x)); }
+
 // Shared words at the start of every group's region: 0-1 shot broadcast
 // (double buffered), 2 the +inf word, 4-11 the per-batch counters.
 constexpr int kMiscWords = 12;
@@ -247,7 +253,7 @@ struct Lane {
     }
 };
 
-template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC>
+template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int RULE>
 struct Decoder {
     using L = Lane<G, PCM, DCM, PVM, CVM, CMIN, RC>;
     static constexpr uint32_t kPass = 4u * CVM * G;   // bytes between variable passes
@@ -294,34 +300,67 @@ struct Decoder {
                 if (p < g.pc) {
                     const bool live = (ln.cvalid >> p) & 1u;
                     uint32_t qb[DCM];
-                    float mn1 = f_inf(), mn2 = f_inf();
                     uint32_t S = ((sbits >> p) & 1u) ? 0x80000001u : 0u;
-#pragma unroll
-                    for (int k = 0; k < DCM; ++k) {
-                        // unused slots point at the group's +inf word
-                        const uint32_t b = lds32(ln.addr(p, k));
-                        qb[k] = b;
-                        S ^= b;   // bit 31: sign parity, bit 0: hard-decision parity
-                        const float av = fabsf(__uint_as_float(b));
-                        mn2 = fminf(mn2, fmaxf(mn1, av));
-                        mn1 = fminf(mn1, av);
-                    }
-                    unsat |= S;
-                    if (scatter) {
-                        // the minimum over the other edges is min2 for the edge
-                        // holding min1 and min1 for all others; with a tie at
-                        // min1 both are equal, so no argmin is needed
-                        const uint32_t Sm = S & 0x80000000u;
-                        uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap)) ^ Sm;
-                        uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap)) ^ Sm;
-                        if (RC && !live) m1 = m2 = 0x7F800000u;   // idle check: writes +inf back
+                    if constexpr (RULE == 0) {
+                        // normalized min-sum
+                        float mn1 = f_inf(), mn2 = f_inf();
 #pragma unroll
                         for (int k = 0; k < DCM; ++k) {
-                            const uint32_t a = ln.addr(p, k);
-                            const bool is_min = fabsf(__uint_as_float(qb[k])) == mn1;
-                            const uint32_t out = (is_min ? m2 : m1) ^ (qb[k] & 0x80000000u);
-                            if (RC) sts32(a, out);
-                            else sts32_if(a, out, a != ln.inf_addr);
+                            // unused slots point at the group's +inf word
+                            const uint32_t b = lds32(ln.addr(p, k));
+                            qb[k] = b;
+                            S ^= b;   // bit 31: sign parity, bit 0: hard-decision parity
+                            const float av = fabsf(__uint_as_float(b));
+                            mn2 = fminf(mn2, fmaxf(mn1, av));
+                            mn1 = fminf(mn1, av);
+                        }
+                        unsat |= S;
+                        if (scatter) {
+                            // the minimum over the other edges is min2 for the edge
+                            // holding min1 and min1 for all others; with a tie at
+                            // min1 both are equal, so no argmin is needed
+                            const uint32_t Sm = S & 0x80000000u;
+                            uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap)) ^ Sm;
+                            uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap)) ^ Sm;
+                            if (RC && !live) m1 = m2 = 0x7F800000u;   // idle check: writes +inf back
+#pragma unroll
+                            for (int k = 0; k < DCM; ++k) {
+                                const uint32_t a = ln.addr(p, k);
+                                const bool is_min = fabsf(__uint_as_float(qb[k])) == mn1;
+                                const uint32_t out = (is_min ? m2 : m1) ^ (qb[k] & 0x80000000u);
+                                if (RC) sts32(a, out);
+                                else sts32_if(a, out, a != ln.inf_addr);
+                            }
+                        }
+                    } else {
+                        // product-sum: r_k = phi(sum_{j != k} phi(|q_j|)) with the
+                        // extrinsic sign; +inf inputs (cut or unused) add phi = 0
+                        float f[DCM];
+#pragma unroll
+                        for (int k = 0; k < DCM; ++k) {
+                            const uint32_t b = lds32(ln.addr(p, k));
+                            qb[k] = b;
+                            S ^= b;
+                            f[k] = phi(fabsf(__uint_as_float(b)));
+                        }
+                        unsat |= S;
+                        if (scatter) {
+                            const uint32_t Sm = S & 0x80000000u;
+                            float suf[DCM + 1];
+                            suf[DCM] = 0.0f;
+#pragma unroll
+                            for (int k = DCM - 1; k >= 0; --k) suf[k] = suf[k + 1] + f[k];
+                            float pre = 0.0f;
+#pragma unroll
+                            for (int k = 0; k < DCM; ++k) {
+                                const uint32_t a = ln.addr(p, k);
+                                float mag = fminf(phi(pre + suf[k + 1]), kLlrCap);
+                                pre += f[k];
+                                if (RC && !live) mag = f_inf();   // idle check: writes +inf back
+                                const uint32_t out = __float_as_uint(mag) ^ Sm ^ (qb[k] & 0x80000000u);
+                                if (RC) sts32(a, out);
+                                else sts32_if(a, out, a != ln.inf_addr);
+                            }
                         }
                     }
                 }
@@ -568,7 +607,7 @@ struct Decoder {
     }
 };
 
-template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int BLOCK, int MINB>
+template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int RULE, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int region_words)
 {
     extern __shared__ uint32_t smem[];
@@ -587,7 +626,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int 
         grp.leader = 0;
     }
     uint32_t *region = smem + (size_t)gib * region_words;
-    Decoder<G, PCM, DCM, PVM, CVM, CMIN, RC>::decode(ld, region, grp, gib);
+    Decoder<G, PCM, DCM, PVM, CVM, CMIN, RC, RULE>::decode(ld, region, grp, gib);
 }
 
 // Cut selection alone, one block per shot (same selection code as the fused kernel).
@@ -663,22 +702,25 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
 // (id, G, check passes, row weight, variable passes, column weight, regular
 // columns, regular rows, block threads, min blocks per SM)
 // (id, G, check passes, row weight, variable passes, column weight, minimum
-// column weight, regular rows, block threads, min blocks per SM)
-#define BPDC_VARIANTS(X)                            \
-    X(0, 32, 3, 6, 5, 3, 3, true, 256, 4)           \
-    X(1, 256, 5, 7, 10, 4, 3, true, 256, 3)         \
-    X(2, 512, 3, 7, 5, 4, 3, true, 512, 2)          \
-    X(3, 256, 4, 8, 11, 3, 2, false, 256, 3)        \
-    X(4, 512, 2, 8, 6, 3, 2, false, 512, 2)         \
-    X(5, 32, 4, 8, 8, 4, 1, false, 256, 4)          \
-    X(6, 128, 10, 7, 20, 4, 3, true, 128, 6)        \
-    X(7, 32, 3, 6, 5, 3, 3, true, 256, 3)           \
-    X(8, 256, 5, 7, 10, 4, 3, true, 256, 2)         \
-    X(9, 512, 3, 7, 5, 4, 3, true, 512, 1)          \
-    X(10, 256, 4, 8, 11, 3, 2, false, 256, 2)
+// column weight, regular rows, check rule (0 min-sum, 1 product-sum), block
+// threads, min blocks per SM)
+#define BPDC_VARIANTS(X)                               \
+    X(0, 32, 3, 6, 5, 3, 3, true, 0, 256, 4)           \
+    X(1, 256, 5, 7, 10, 4, 3, true, 0, 256, 3)         \
+    X(2, 512, 3, 7, 5, 4, 3, true, 0, 512, 2)          \
+    X(3, 256, 4, 8, 11, 3, 2, false, 0, 256, 3)        \
+    X(4, 512, 2, 8, 6, 3, 2, false, 0, 512, 2)         \
+    X(5, 32, 4, 8, 8, 4, 1, false, 0, 256, 4)          \
+    X(6, 128, 10, 7, 20, 4, 3, true, 0, 128, 6)        \
+    X(7, 32, 3, 6, 5, 3, 3, true, 0, 256, 3)           \
+    X(8, 256, 5, 7, 10, 4, 3, true, 0, 256, 2)         \
+    X(9, 512, 3, 7, 5, 4, 3, true, 0, 512, 1)          \
+    X(10, 256, 4, 8, 11, 3, 2, false, 0, 256, 2)       \
+    X(11, 32, 4, 4, 4, 2, 1, false, 1, 256, 4)         \
+    X(12, 32, 3, 6, 5, 3, 3, true, 1, 256, 4)
 
 static const Variant kVariants[] = {
-#define X(id, G, PC, DC, PV, CV, CMIN, RC, BLK, MB) {id, G, PC, DC, PV, CV, CMIN, RC, BLK, MB},
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB) {id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB},
     BPDC_VARIANTS(X)
 #undef X
 };
@@ -689,8 +731,8 @@ const Variant &variant(int id) { return kVariants[id]; }
 static const void *variant_fn(int id)
 {
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, CMIN, RC, BLK, MB) \
-    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, CMIN, RC, BLK, MB>;
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB) \
+    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB>;
         BPDC_VARIANTS(X)
 #undef X
     default: return nullptr;
@@ -739,9 +781,9 @@ cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_byte
 {
     const int region = smem_bytes / 4 / (kVariants[id].block_threads / kVariants[id].G);
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, CMIN, RC, BLK, MB)                                                     \
-    case id:                                                                                            \
-        decode_kernel<G, PC, DC, PV, CV, CMIN, RC, BLK, MB><<<grid, BLK, smem_bytes, s>>>(ld, region); \
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB)                                                     \
+    case id:                                                                                                  \
+        decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB><<<grid, BLK, smem_bytes, s>>>(ld, region); \
         return cudaGetLastError();
         BPDC_VARIANTS(X)
 #undef X

@@ -68,8 +68,8 @@ def test_argument_validation(lib):
               _bpdc.Options(max_iter=70000), _bpdc.Options(dc_enable=2), _bpdc.Options(tie_rel=-1.0)):
         rc, _ = _create(lib, H, L, D, p, o)
         assert rc == _bpdc.ERR_INVALID_ARG, o
-    rc, _ = _create(lib, H, L, D, p, _bpdc.Options(variant=1))
-    assert rc == _bpdc.ERR_UNSUPPORTED
+    rc, _ = _create(lib, H, L, D, p, _bpdc.Options(variant=2))
+    assert rc == _bpdc.ERR_INVALID_ARG
     # malformed CSR: duplicate column, column out of range, bad row_ptr
     ptr = np.array([0, 2, 4], np.int32)
     for col in (np.array([0, 0, 1, 2], np.int32), np.array([0, 1, 1, 3], np.int32)):

@@ -36,8 +36,9 @@ def _run(pkg, oracle_mod, P, B, opts_kw, seed=SEED, offset=0, G=None, persistent
         g.set_plan(G)
     out = g.decode(to_dev(s), offset, obs_true=to_dev(o), persistent=persistent)
     g.sync_status()
-    oo = oracle_mod.Options(alpha=opts.ms_scale, max_iter=opts.max_iter, dc_enable=opts.dc_enable,
-                            dc_prior=opts.dc_prior, tie_rel=opts.tie_rel, tie_seed=opts.tie_seed)
+    oo = oracle_mod.Options(variant=opts.variant, alpha=opts.ms_scale, max_iter=opts.max_iter,
+                            dc_enable=opts.dc_enable, dc_prior=opts.dc_prior, tie_rel=opts.tie_rel,
+                            tie_seed=opts.tie_seed)
     ref = oracle_mod.decode_batch(P, s, offset, oo, want_post=True, want_post1=True, want_cut=True)
     ref["well_conditioned"] = well_conditioned(oracle_mod, P, s, offset, oo, ref)
     return g, s, o, out, ref
@@ -129,6 +130,46 @@ def test_alpha_one_parity(pkg, oracle_mod):
     pert = oracle_mod.decode_batch(Q, s, 0, oracle_mod.Options(alpha=1.0, max_iter=72))
     fail_p = int(((pert["status"] == 2) | (pert["obs_pred"] != o).any(1)).sum())
     assert within_2_sigma(rep["fail_gpu"], fail_p, rep["B"]), (rep["fail_gpu"], fail_p)
+
+
+@pytest.mark.parametrize("d,p,prior", [(7, 0.01, 1), (7, 0.05, 1), (5, 0.06, 0)])
+def test_surface_code_product_sum_parity(pkg, oracle_mod, d, p, prior):
+    """The paper's surface-code setting: product-sum BP, T_iter = n, second BP
+    on the first-run posterior (Sec. III.B)."""
+    P = bi.surface_problem(d, p)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 6000, dict(variant=1, max_iter=d * d, dc_prior=prior))
+    assert g.info["kernel_id"] == 11
+    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.8)
+
+
+def test_bb72_product_sum_parity(pkg, oracle_mod):
+    P = bi.bb_problem("bb72", 0.05)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, dict(variant=1, max_iter=50))
+    assert g.info["kernel_id"] == 12
+    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.8)
+
+
+def test_surface_code_min_sum_parity(pkg, oracle_mod):
+    P = bi.surface_problem(7, 0.04)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, dict(ms_scale=0.625, max_iter=49, dc_prior=1))
+    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.5)
+
+
+def test_product_sum_posteriors(pkg, oracle_mod):
+    P = bi.surface_problem(7, 0.03)
+    _, s, _ = sample_shots(P, SEED + 9, 0, 3000)
+    g = pkg.Graph.from_problem(P, pkg.Options(variant=1, max_iter=49, dc_prior=1))
+    out = g.decode(to_dev(s), 0, posterior=True)
+    oo = oracle_mod.Options(variant=1, max_iter=49, dc_prior=1)
+    ref = oracle_mod.decode_batch(P, s, 0, oo, want_post=True, want_post1=True)
+    ref["well_conditioned"] = well_conditioned(oracle_mod, P, s, 0, oo, ref)
+    comp = comparable(P, ref, 1e-5) & ref["well_conditioned"] & (ref["status"] == 0)
+    assert comp.sum() > 1000
+    rp, gp = ref["post"][comp], out["posterior_llr"].cpu().numpy().astype(np.float64)[comp]
+    inf = np.isinf(rp)
+    assert (np.isinf(gp) == inf).all()
+    rel = np.abs(gp[~inf] - rp[~inf]) / np.maximum(np.abs(rp[~inf]), 1.0)
+    assert rel.max() < 1e-4, rel.max()
 
 
 # ---------------------------------------------------------------------------

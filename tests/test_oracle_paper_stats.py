@@ -70,3 +70,65 @@ def test_table3_flatness_fractions(bb144_run):
     for eps, pct in zip((0.1, 0.2, 0.3, 0.4, 0.5), expect):
         got = 100.0 * (deltas <= eps).mean()
         assert abs(got - pct) < 5.0, (eps, got, pct)
+
+
+# ---------------------------------------------------------------------------
+# Surface code [[49,1,7]]: product-sum BP, T_iter = n = 49 (Fig. 2 caption),
+# second BP on the first-run posterior (Algorithm 1 as printed; Sec. III.B says
+# the priors p degrade surface codes).
+
+SURFACE_SHOTS = 1_000_000
+
+
+@pytest.fixture(scope="module")
+def surface_run(oracle_mod):
+    P = bi.surface_problem(7, 0.01)
+    _, s, o = sample_shots(P, 0x2510086950 + 200, 0, SURFACE_SHOTS)
+    idx = np.nonzero(s.any(1))[0]
+    opts = oracle_mod.Options(variant=1, max_iter=49, dc_prior=1)
+    out = oracle_mod.decode_batch(P, s[idx], 0, opts, want_post1=True)
+    return P, s, o, idx, out
+
+
+@pytest.mark.slow
+def test_table2_surface_code_counts(surface_run):
+    P, s, o, idx, out = surface_run
+    shots, bp_failed, _, both_fail, _, osd_only = _row("table2_overlap.txt", "surface49")
+    st = out["status"]
+    frac = (st > 0).sum() / SURFACE_SHOTS
+    exp_frac = bp_failed / shots
+    assert abs(frac - exp_frac) < 4 * np.sqrt(exp_frac * (1 - exp_frac) / SURFACE_SHOTS), (frac, exp_frac)
+    n_dc = int(((st == 2) | (out["obs_pred"] != o[idx]).any(1)).sum())
+    exp_dc = (both_fail + osd_only) / shots * SURFACE_SHOTS
+    assert abs(n_dc - exp_dc) < 4 * np.sqrt(exp_dc), (n_dc, exp_dc)
+
+
+@pytest.mark.slow
+def test_table3_surface_flatness(surface_run):
+    P, s, o, idx, out = surface_run
+    expect = _row("table3_flatness.txt", "surface49")
+    failed = out["status"] > 0
+    with np.errstate(over="ignore"):
+        ph = 1.0 / (1.0 + np.exp(out["post1"][failed][:5000]))
+    D = P.D.toarray().astype(bool)
+    deltas = np.concatenate([[ph[b, r].max() - ph[b, r].min() for r in D] for b in range(ph.shape[0])])
+    for eps, pct in zip((0.1, 0.2, 0.3, 0.4, 0.5), expect):
+        assert abs(100.0 * (deltas <= eps).mean() - pct) < 2.0, (eps, pct)
+
+
+def test_surface_code_construction():
+    from bpdc_inputs import gf2
+    for d in (3, 5, 7):
+        hx, hz, oz = bi._surface(d)
+        n = d * d
+        assert hx.shape == hz.shape == ((n - 1) // 2, n)
+        assert not ((hz.astype(int) @ hx.T) % 2).any() and oz.shape[0] == 1
+        assert hx.sum(1).max() == 4 and hx.sum(0).max() == 2 and hz.sum(0).max() == 2
+        assert oz.sum(1).min() >= d
+    # distance 3 for d = 3 by brute force (Sec. II.B.1: [[d^2, 1, d]])
+    import itertools
+    hx, hz, _ = bi._surface(3)
+    found = min(w for w in range(1, 10) for sup in itertools.combinations(range(9), w)
+                if not ((hx.astype(int)[:, list(sup)].sum(1)) % 2).any()
+                and not gf2.in_rowspace(hz, np.isin(np.arange(9), sup).astype(np.uint8)))
+    assert found == 3
