@@ -9,7 +9,8 @@ Acceptance (FP32 GPU vs FP64 oracle):
     candidate set);
   * and the shot is *well conditioned*: the oracle's outcome (status, e_hat,
     iteration counts) does not change when every prior is multiplied by
-    1 + 1e-6 * z_j (z_j standard normal, three independent draws).  Min-sum
+    1 + eps * z_j (z_j standard normal; three draws each at eps = 1e-7, 1e-6
+    and 1e-5, the scale of FP32 rounding).  Min-sum
     with uniform priors is full of exact ties and exact zero messages; on the
     shots where such a tie decides the outcome, any rounding difference
     (FP32 against FP64) may decide it differently, so those shots are
@@ -55,12 +56,14 @@ def robust_rows(D, post1: np.ndarray, tie_rel: float) -> np.ndarray:
 
 
 def well_conditioned(oracle_mod, problem, syn, shot_offset, opts, ref, draws: int = 3,
-                     eps: float = 1e-6) -> np.ndarray:
-    """bool [B]: the oracle outcome survives tiny random relative prior perturbations."""
+                     eps=(1e-7, 1e-6, 1e-5)) -> np.ndarray:
+    """bool [B]: the oracle outcome survives tiny random relative prior
+    perturbations (``draws`` draws at each relative size in ``eps``)."""
     ok = np.ones(syn.shape[0], dtype=bool)
-    for d in range(draws):
+    for d in range(draws * len(eps)):
         rng = np.random.default_rng(1000 + d)
-        q = problem.with_priors(np.clip(problem.priors * (1 + eps * rng.standard_normal(problem.N)),
+        e = eps[d % len(eps)]
+        q = problem.with_priors(np.clip(problem.priors * (1 + e * rng.standard_normal(problem.N)),
                                         1e-300, 0.5))
         pert = oracle_mod.decode_batch(q, syn, shot_offset, opts)
         ok &= ((pert["status"] == ref["status"]) & (pert["e_hat"] == ref["e_hat"]).all(1)
