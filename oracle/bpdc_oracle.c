@@ -16,7 +16,10 @@
  *     the hard decision reproduces the syndrome, else after T_iter
  *     iterations.
  *   - Check rules (Sec. II.C.1 cites them): normalized min-sum and
- *     product-sum, written per edge from their definitions, O(d^2) per check.
+ *     product-sum, written per edge from their definitions, O(d^2) per check;
+ *     the product-sum value 2 atanh(prod tanh(q/2)) is evaluated as
+ *     phi(sum phi(|q|)), phi(x) = -log tanh(x/2), so that it stays exact
+ *     where tanh(q/2) would round to 1 (|q| above about 37 in FP64).
  *   - Algorithm 1: run BP; if it fails, for every row of the degeneracy
  *     matrix D pick the support variable of lowest posterior error
  *     probability (= highest posterior LLR), take the union of the picks,
@@ -124,6 +127,10 @@ static void tanner_free(tanner *g)
 
 static double sgn(double x) { return x < 0.0 ? -1.0 : 1.0; }
 
+/* phi(x) = -log(tanh(x / 2)) = log(1 + 2 / (e^x - 1)) for x >= 0; phi(0) = +inf,
+ * phi(+inf) = 0, and phi(phi(x)) = x. */
+static double phi(double x) { return log1p(2.0 / expm1(x)); }
+
 /* Check-to-variable message on edge e of check i: the check tells its
  * variable what the parity constraint s_i implies given the messages arriving
  * on all of its *other* edges. */
@@ -142,15 +149,18 @@ static double check_message(const tanner *g, int i, int e, int s_i, const double
         if (mag > ORACLE_LLR_CAP) mag = ORACLE_LLR_CAP;
         return alpha * sign * mag;
     } else {
-        /* product-sum: (-1)^s_i * 2 atanh( prod tanh(q / 2) ) */
-        double prod = 1.0;
+        /* product-sum: (-1)^s_i * sign * 2 atanh( prod |tanh(q / 2)| ), written as
+         * phi( sum phi(|q|) ) with phi(x) = -log tanh(x / 2) (the same function;
+         * this form does not saturate where tanh(x / 2) rounds to 1) */
+        double sign = syn_sign, sum = 0.0;
         for (int f = g->row_ptr[i]; f < g->row_ptr[i + 1]; ++f) {
             if (f == e) continue;
-            prod *= tanh(q[f] / 2.0);
+            sign *= sgn(q[f]);
+            sum += phi(fabs(q[f]));
         }
-        double mag = 2.0 * atanh(fabs(prod));
+        double mag = phi(sum);
         if (!(mag < ORACLE_LLR_CAP)) mag = ORACLE_LLR_CAP;
-        return syn_sign * sgn(prod) * mag;
+        return sign * mag;
     }
 }
 

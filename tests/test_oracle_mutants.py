@@ -20,15 +20,15 @@ MUTANTS = {
     "syndrome_sign_dropped": ("double syn_sign = s_i ? -1.0 : 1.0;", "double syn_sign = 1.0;"),
     "variable_message_not_extrinsic": ("if (b != a) ext += r[g->col_edges[b]];",
                                        "ext += r[g->col_edges[b]];"),
-    "check_message_includes_own_edge": ("if (f == e) continue;\n            sign *= sgn(q[f]);",
-                                        "sign *= sgn(q[f]);"),
+    "check_message_includes_own_edge": ("if (f == e) continue;\n            sign *= sgn(q[f]);\n            if (fabs",
+                                        "sign *= sgn(q[f]);\n            if (fabs"),
     "prior_llr_inverted": ("return log((1.0 - p) / p);", "return log(p / (1.0 - p));"),
     "min_sum_scale_dropped": ("return alpha * sign * mag;", "return sign * mag;"),
     "hard_decision_flipped": ("e_hat[j] = post[j] <= 0.0;   /* Eq. 4 */",
                               "e_hat[j] = post[j] >= 0.0;"),
     "cut_most_likely_error": ("if (post[P->d_col[a]] >= thr) cand[nc++] = P->d_col[a];",
                               "if (post[P->d_col[a]] < thr) cand[nc++] = P->d_col[a];"),
-    "tanh_without_half": ("prod *= tanh(q[f] / 2.0);", "prod *= tanh(q[f]);"),
+    "phi_of_signed_message": ("sum += phi(fabs(q[f]));", "sum += phi(q[f]);"),
     "second_bp_keeps_cut_columns": ("for (int j = 0; j < N; ++j) keep[j] = cut[j] ? -1 : nk++;",
                                     "for (int j = 0; j < N; ++j) keep[j] = nk++;"),
 }
