@@ -17,9 +17,11 @@
  *     iterations.
  *   - Check rules (Sec. II.C.1 cites them): normalized min-sum and
  *     product-sum, written per edge from their definitions, O(d^2) per check;
- *     the product-sum value 2 atanh(prod tanh(q/2)) is evaluated as
- *     phi(sum phi(|q|)), phi(x) = -log tanh(x/2), so that it stays exact
- *     where tanh(q/2) would round to 1 (|q| above about 37 in FP64).
+ *     the product-sum value 2 atanh(prod tanh(q/2)) is folded over the other
+ *     edges with the pairwise rule a [+] b = 2 atanh(tanh(a/2) tanh(b/2)) in
+ *     its log form min(a,b) + log(1 + e^-(a+b)) - log(1 + e^-|a-b|), which
+ *     stays exact at every magnitude up to the cap (tanh(q/2) rounds to 1
+ *     above |q| ~ 37 in FP64, and -log tanh(q/2) underflows above ~709).
  *   - Algorithm 1: run BP; if it fails, for every row of the degeneracy
  *     matrix D pick the support variable of lowest posterior error
  *     probability (= highest posterior LLR), take the union of the picks,
@@ -127,9 +129,17 @@ static void tanner_free(tanner *g)
 
 static double sgn(double x) { return x < 0.0 ? -1.0 : 1.0; }
 
-/* phi(x) = -log(tanh(x / 2)) = log(1 + 2 / (e^x - 1)) for x >= 0; phi(0) = +inf,
- * phi(+inf) = 0, and phi(phi(x)) = x. */
-static double phi(double x) { return log1p(2.0 / expm1(x)); }
+/* Magnitude of the product-sum of two messages of magnitudes a, b >= 0:
+ * 2 atanh(tanh(a/2) tanh(b/2)) = log((1 + e^-(a+b)) / (e^-a + e^-b)), which
+ * rearranges to min(a,b) + log(1 + e^-(a+b)) - log(1 + e^-|a-b|).  +inf is
+ * the identity (a cut or absent neighbour), and the result lies in
+ * [0, min(a,b)]. */
+static double boxplus(double a, double b)
+{
+    double d = (a == b) ? 0.0 : fabs(a - b);
+    double r = fmin(a, b) + log1p(exp(-(a + b))) - log1p(exp(-d));
+    return r > 0.0 ? r : 0.0;
+}
 
 /* Check-to-variable message on edge e of check i: the check tells its
  * variable what the parity constraint s_i implies given the messages arriving
@@ -149,16 +159,14 @@ static double check_message(const tanner *g, int i, int e, int s_i, const double
         if (mag > ORACLE_LLR_CAP) mag = ORACLE_LLR_CAP;
         return alpha * sign * mag;
     } else {
-        /* product-sum: (-1)^s_i * sign * 2 atanh( prod |tanh(q / 2)| ), written as
-         * phi( sum phi(|q|) ) with phi(x) = -log tanh(x / 2) (the same function;
-         * this form does not saturate where tanh(x / 2) rounds to 1) */
-        double sign = syn_sign, sum = 0.0;
+        /* product-sum: (-1)^s_i * sign * 2 atanh( prod |tanh(q / 2)| ), the
+         * product taken pairwise with boxplus (the empty product is +inf) */
+        double sign = syn_sign, mag = INFINITY;
         for (int f = g->row_ptr[i]; f < g->row_ptr[i + 1]; ++f) {
             if (f == e) continue;
             sign *= sgn(q[f]);
-            sum += phi(fabs(q[f]));
+            mag = boxplus(mag, fabs(q[f]));
         }
-        double mag = phi(sum);
         if (!(mag < ORACLE_LLR_CAP)) mag = ORACLE_LLR_CAP;
         return sign * mag;
     }

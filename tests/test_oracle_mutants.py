@@ -28,7 +28,8 @@ MUTANTS = {
                               "e_hat[j] = post[j] >= 0.0;"),
     "cut_most_likely_error": ("if (post[P->d_col[a]] >= thr) cand[nc++] = P->d_col[a];",
                               "if (post[P->d_col[a]] < thr) cand[nc++] = P->d_col[a];"),
-    "phi_of_signed_message": ("sum += phi(fabs(q[f]));", "sum += phi(q[f]);"),
+    "boxplus_of_signed_message": ("mag = boxplus(mag, fabs(q[f]));", "mag = boxplus(mag, q[f]);"),
+    "boxplus_sign_of_correction": ("log1p(exp(-(a + b))) - log1p(exp(-d))", "log1p(exp(-(a + b))) + log1p(exp(-d))"),
     "second_bp_keeps_cut_columns": ("for (int j = 0; j < N; ++j) keep[j] = cut[j] ? -1 : nk++;",
                                     "for (int j = 0; j < N; ++j) keep[j] = nk++;"),
 }

@@ -60,6 +60,28 @@ def test_product_sum_exact_on_trees(oracle_mod, seed):
     np.testing.assert_allclose(post, exact, rtol=1e-9, atol=1e-9)
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_product_sum_exact_on_trees_at_huge_llrs(oracle_mod, seed):
+    """Priors of 1e-300 .. 1e-200 (LLRs 460 .. 690) so that messages on the tree
+    exceed 700, where -log tanh(x/2) underflows FP64; the exact marginals
+    come from log-sum-exp over all syndrome-consistent errors."""
+    from scipy.special import logsumexp
+    rng = np.random.default_rng(500 + seed)
+    P = random_tree_problem(rng, n_checks=int(rng.integers(2, 6)))
+    P = P.with_priors(10.0 ** rng.uniform(-300, -200, size=P.N))
+    H = P.H.toarray()
+    e = np.zeros(P.N, np.uint8)
+    e[rng.choice(P.N, size=seed % 2, replace=False)] = 1
+    s = (H.astype(int) @ e) % 2
+    errs, logw = brute_force(H, P.priors, s)
+    exact = np.array([logsumexp(logw[errs[:, j] == 0]) - logsumexp(logw[errs[:, j] == 1])
+                      for j in range(P.N)])
+    assert np.abs(exact).max() > 709
+    opts = oracle_mod.Options(variant=1, max_iter=2 * P.N + 2)
+    _, _, post, _ = oracle_mod.bp(P, s, opts=opts, early_stop=False)
+    np.testing.assert_allclose(post, exact, rtol=1e-9, atol=1e-9)
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_min_sum_exact_min_energy_on_trees(oracle_mod, seed):
     rng = np.random.default_rng(100 + seed)
