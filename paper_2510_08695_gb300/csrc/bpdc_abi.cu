@@ -205,7 +205,17 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     for (int j = 0; j < N; ++j) {
         const int pos = lay.pos_of_var[j];
         P.var_deg[pos] = (uint8_t)deg[j];
-        P.lam[pos] = (float)std::log((1.0 - g.priors[j]) / g.priors[j]);
+        // The decoder keeps each variable's hard decision in the mantissa LSB
+        // of the messages it sends.  Priors are stored with that bit clear,
+        // so the first messages carry lambda unchanged and exact identities
+        // of the rule (lambda - lambda = 0 through a two-input check) are
+        // not moved off zero by the tag; the change is at most one ulp.
+        float lam = (float)std::log((1.0 - g.priors[j]) / g.priors[j]);
+        uint32_t lb;
+        std::memcpy(&lb, &lam, 4);
+        lb &= ~1u;
+        std::memcpy(&lam, &lb, 4);
+        P.lam[pos] = lam;
         P.pos_col[pos] = j;
     }
     P.d_ptr.assign(Md + 1, 0);

@@ -145,6 +145,14 @@ __device__ __forceinline__ void cut_rows(const DevGraph &g, uint64_t gshot, int 
 // accurate: expm1 and log1p avoid the cancellations of tanh near 1.
 __device__ __forceinline__ float phi(float x) { return log1pf(2.0f / expm1f(x)); }
 
+// phi(x) = 2 atanh(e^-x) falls below the smallest normal FP32 number once
+// x > ~87, so a sum of phi terms whose smallest argument m is large would
+// vanish and its phi would come out +inf.  Sums are therefore taken with every
+// argument lowered by s = max(0, m - kPhiShift): where s > 0 every argument is
+// >= kPhiShift, phi(x) = 2 e^-x to within a relative e^-2x, and
+// phi(sum_j phi(x_j)) = -log sum_j e^-x_j + O(e^-2m), which lowers by exactly s.
+constexpr float kPhiShift = 20.0f;
+
 // Shared words at the start of every group's region: 0-1 shot broadcast
 // (double buffered), 2 the +inf word, 4-11 the per-batch counters.
 constexpr int kMiscWords = 12;
@@ -334,18 +342,45 @@ struct Decoder {
                         }
                     } else {
                         // product-sum: r_k = phi(sum_{j != k} phi(|q_j|)) with the
-                        // extrinsic sign; +inf inputs (cut or unused) add phi = 0
-                        float f[DCM];
+                        // extrinsic sign; +inf inputs (cut or unused) add phi = 0.
+                        // The smallest argument of edge k's sum is min2 on the
+                        // (unique) minimum edge and min1 on every other edge.
+                        // With at most two finite inputs (min3 = +inf) every
+                        // extrinsic set holds one finite value, and the rule
+                        // returns it unchanged: that case takes the exact
+                        // value instead of phi(phi(x)), which FP32 rounds.
+                        float mn1 = f_inf(), mn2 = f_inf(), mn3 = f_inf();
 #pragma unroll
                         for (int k = 0; k < DCM; ++k) {
                             const uint32_t b = lds32(ln.addr(p, k));
                             qb[k] = b;
                             S ^= b;
-                            f[k] = phi(fabsf(__uint_as_float(b)));
+                            const float av = fabsf(__uint_as_float(b));
+                            mn3 = fminf(mn3, fmaxf(mn2, av));
+                            mn2 = fminf(mn2, fmaxf(mn1, av));
+                            mn1 = fminf(mn1, av);
                         }
                         unsat |= S;
                         if (scatter) {
+                            const bool pair = mn3 == f_inf();
                             const uint32_t Sm = S & 0x80000000u;
+                            const float sa = fminf(fmaxf(mn1 - kPhiShift, 0.0f), kLlrCap);
+                            const float sb = fminf(fmaxf(mn2 - kPhiShift, 0.0f), kLlrCap);
+                            float f[DCM];
+#pragma unroll
+                            for (int k = 0; k < DCM; ++k) f[k] = phi(fabsf(__uint_as_float(qb[k])) - sa);
+                            // the minimum edge's own sum, needed only when its
+                            // shift differs (min2 > min1 and min2 > kPhiShift)
+                            float rb = 0.0f;
+                            if (sb != sa) {
+                                float sum = 0.0f;
+#pragma unroll
+                                for (int k = 0; k < DCM; ++k) {
+                                    const float av = fabsf(__uint_as_float(qb[k]));
+                                    sum += av == mn1 ? 0.0f : phi(av - sb);
+                                }
+                                rb = sb + phi(sum);
+                            }
                             float suf[DCM + 1];
                             suf[DCM] = 0.0f;
 #pragma unroll
@@ -354,7 +389,11 @@ struct Decoder {
 #pragma unroll
                             for (int k = 0; k < DCM; ++k) {
                                 const uint32_t a = ln.addr(p, k);
-                                float mag = fminf(phi(pre + suf[k + 1]), kLlrCap);
+                                const bool is_min = fabsf(__uint_as_float(qb[k])) == mn1;
+                                const bool own_b = sb != sa && is_min;
+                                float mag = pair ? (is_min ? mn2 : mn1)
+                                                 : (own_b ? rb : sa + phi(pre + suf[k + 1]));
+                                mag = fminf(mag, kLlrCap);
                                 pre += f[k];
                                 if (RC && !live) mag = f_inf();   // idle check: writes +inf back
                                 const uint32_t out = __float_as_uint(mag) ^ Sm ^ (qb[k] & 0x80000000u);

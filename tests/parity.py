@@ -99,6 +99,11 @@ def compare(problem, gpu_out: dict, ref: dict, obs: np.ndarray | None, tie_rel: 
     rep = dict(B=len(st), comparable=int(comp.sum()), mismatched=np.nonzero(comp & ~same)[0],
                identical_all=int(same.sum()), status_gpu=np.bincount(st, minlength=3),
                status_ref=np.bincount(ref["status"], minlength=3))
+    # what differs on the first few mismatched shots (for the assertion message)
+    rep["details"] = [dict(shot=int(b), status=(int(st[b]), int(ref["status"][b])),
+                           iters=((int(it1[b]), int(it2[b])), (int(ref["iters1"][b]), int(ref["iters2"][b]))),
+                           e_diff=np.nonzero(e[b] != ref["e_hat"][b])[0].tolist())
+                      for b in rep["mismatched"][:5]]
     if obs is not None:
         fail_g = (st == 2) | (f != obs).any(1)
         fail_o = (ref["status"] == 2) | (ref["obs_pred"] != obs).any(1)
