@@ -238,6 +238,19 @@ int bpdc_sample(bpdc_graph_t g, int64_t B, uint64_t seed, uint64_t shot_offset,
  * clears it. */
 int bpdc_graph_sync_status(bpdc_graph_t g, void *stream);
 
+/* Shared-memory bandwidth of device `device`, the roof of the decode kernels
+ * (their messages stay in shared memory; one 4-byte load and one 4-byte store
+ * per message per phase).  Runs a microbenchmark of conflict-free 4-byte
+ * loads and stores (8 + 8 per thread and iteration, `reps` iterations,
+ * reps >= 8, two 1024-thread blocks on every SM, about 0.5 us per iteration)
+ * three times after a warm-up run and reports the best: bytes moved per
+ * second (CUDA events around the launch), bytes per SM clock cycle (from the
+ * blocks' own cycle counters) and the SM clock those imply, plus the number
+ * of SMs.  Synchronous; allocates and frees a few bytes of device memory.
+ * Errors: BPDC_ERR_INVALID_ARG (NULL output, reps < 8), BPDC_ERR_CUDA. */
+int bpdc_measure_smem_peak(int32_t device, int32_t reps, double *bytes_per_second,
+                           double *bytes_per_sm_clock, double *sm_clock_hz, int32_t *num_sms);
+
 /* Gradient of a weighted-BP loss (differentiable weighted BP).  Not
  * implemented: always returns BPDC_ERR_UNSUPPORTED. */
 int bpdc_decode_backward(bpdc_graph_t g, int64_t B, const uint32_t *syndromes,

@@ -112,3 +112,12 @@ def test_valid_problem_needs_a_device_or_succeeds(lib):
         assert lib.bpdc_graph_destroy(out) == 0
     else:
         assert rc in (_bpdc.ERR_CUDA, _bpdc.ERR_INVALID_ARG)
+
+
+def test_smem_peak_rejects_bad_arguments(lib):
+    d = ctypes.c_double()
+    n = ctypes.c_int32()
+    assert lib.bpdc_measure_smem_peak(0, 100, None, ctypes.byref(d), ctypes.byref(d), ctypes.byref(n)) \
+        == _bpdc.ERR_INVALID_ARG
+    assert lib.bpdc_measure_smem_peak(0, 4, ctypes.byref(d), ctypes.byref(d), ctypes.byref(d),
+                                      ctypes.byref(n)) == _bpdc.ERR_INVALID_ARG

@@ -332,3 +332,13 @@ def test_posterior_output(pkg, oracle_mod):
     worst = [(int(np.nonzero(comp)[0][b]), int(j), float(gp[b, j]), float(rp[b, j]))
              for b, j in np.argwhere(rel > 1e-4)[:5]]
     assert rel.max() < 1e-4, (rel.max(), worst)
+
+
+def test_smem_peak_microbenchmark(pkg):
+    """The roof the bench divides by: conflict-free 4-byte shared-memory
+    traffic moves at most 128 B per SM clock (32 banks x 4 B)."""
+    import torch
+    m = pkg.measure_smem_peak(0, reps=4000)
+    assert m["num_sms"] == torch.cuda.get_device_properties(0).multi_processor_count
+    assert 64.0 < m["bytes_per_sm_clock"] <= 128.5, m
+    assert 0.5e9 < m["sm_clock_hz"] < 3.0e9, m
