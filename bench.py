@@ -39,6 +39,7 @@ P_VALUES = [round(0.01 * i, 2) for i in range(1, 11)]
 CODES = ["bb144", "bb72", "hgp2500"]
 ALPHA, T_ITER = 0.625, 50
 SMEM_BYTES_PER_CLK_PER_SM = 128   # 32 banks x 4 B
+SERVE_ROUNDS, SERVE_P, SERVE_T_ITER, SERVE_REQUESTS = 12, 1e-3, 1000, 600
 EDGE_UPDATE_BYTES = 16            # 2 x 4 B read + 2 x 4 B written per edge and iteration
 
 
@@ -411,16 +412,22 @@ def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
     e2e = len(batches) * args.shots_per_point * args.steps / (t0.elapsed_time(t1) / 1e3)
     line["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # ---- serving: seeded Poisson trace of BB72 / BB144 requests of 1..1024 shots
+    # ---- serving: seeded Poisson trace mixing circuit-level BB[[144,12,12]]
+    # requests (12 rounds, p = 1e-3, T_iter = 1000) with code-capacity
+    # BB[[72,12,6]] requests (p = 0.05), 1..1024 shots each
     from paper_2510_08695_gb300 import serving
-    small = [b for b in batches if b["code"] in ("bb72", "bb144") and b["p"] == 0.05]
-    graphs = [b["graph"] for b in small]
-    pools = [b["syndromes"][:200000].cpu().pin_memory() for b in small]
-    calib = serving.poisson_trace(300, rate_per_s=1e9, n_graphs=len(graphs), seed=11)
+    from bpdc_inputs import circuit
+    Pc = circuit.circuit_level_problem("bb144", SERVE_ROUNDS, SERVE_P)
+    gc = pkg.Graph.from_problem(Pc, pkg.Options(ms_scale=ALPHA, max_iter=SERVE_T_ITER))
+    bb72 = [b for b in batches if b["code"] == "bb72" and b["p"] == 0.05][0]
+    graphs = [gc, bb72["graph"]]
+    pools = [gc.sample(60000, SEED + 50, 0)[0].cpu().pin_memory(),
+             bb72["syndromes"][:200000].cpu().pin_memory()]
+    calib = serving.poisson_trace(60, rate_per_s=1e9, n_graphs=len(graphs), seed=11)
     cal = serving.replay(serving.PlainDecoder(graphs), calib, pools)
     service_s = (max(r.done for r in cal) - min(r.arrival for r in cal)) / len(cal)
     rate = 0.7 / service_s
-    trace = serving.poisson_trace(4000, rate_per_s=rate, n_graphs=len(graphs), seed=12)
+    trace = serving.poisson_trace(SERVE_REQUESTS, rate_per_s=rate, n_graphs=len(graphs), seed=12)
     lat = {}
     served = {}
     for name, eng in (("plain", serving.PlainDecoder(graphs)), ("server", serving.Server(graphs, slots=4))):
@@ -433,11 +440,16 @@ def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
         served[name] = reqs
     same = all(torch.equal(a.result[k], b.result[k]) for a, b in zip(served["plain"], served["server"])
                for k in ("corrections", "status", "logical_flips"))
-    line["serving"] = {"trace": f"{len(trace)} Poisson requests of 1..1024 shots over BB[[72,12,6]] and "
-                                f"BB[[144,12,12]] at p=0.05, {rate:.0f} requests/s (70% of the plain decoder's "
-                                "capacity); latency = arrival to results on the host",
+    st = torch.cat([r.result["status"] for r in served["server"] if r.graph_id == 0])
+    line["serving"] = {"trace": f"{len(trace)} Poisson requests of 1..1024 shots, half circuit-level "
+                                f"BB[[144,12,12]] ({SERVE_ROUNDS} rounds, p={SERVE_P:g}, detector model "
+                                f"{Pc.M}x{Pc.N} derived from the depth-8 syndrome circuit, H_DDM w=3, "
+                                f"T_iter={SERVE_T_ITER}) and half code-capacity BB[[72,12,6]] at p=0.05; "
+                                f"{rate:.0f} requests/s (70% of the plain decoder's capacity); latency = arrival "
+                                "to results on the host",
                        "plain_per_request_kernel": lat["plain"], "continuous_batching_server": lat["server"],
-                       "server_slots": 4, "identical_results": same}
+                       "server_slots": 4, "identical_results": same,
+                       "circuit_level_status_counts": torch.bincount(st.long(), minlength=3).tolist()}
     line["p99_us_per_shot"] = lat["server"]["p99_us"]
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample of the workload

@@ -242,7 +242,8 @@ int bpdc_graph_sync_status(bpdc_graph_t g, void *stream);
  * (their messages stay in shared memory; one 4-byte load and one 4-byte store
  * per message per phase).  Runs a microbenchmark of conflict-free 4-byte
  * loads and stores (8 + 8 per thread and iteration, `reps` iterations,
- * reps >= 8, two 1024-thread blocks on every SM, about 0.5 us per iteration)
+ * reps >= 8, one wave of as many 1024-thread blocks per SM as fit with 64 KB
+ * of shared memory each, about 0.5 us per iteration)
  * three times after a warm-up run and reports the best: bytes moved per
  * second (CUDA events around the launch), bytes per SM clock cycle (from the
  * blocks' own cycle counters) and the SM clock those imply, plus the number

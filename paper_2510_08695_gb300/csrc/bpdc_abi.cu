@@ -176,9 +176,14 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     int region = 12 + P.slots + P.cmw + std::max(P.KW, 1);   // 12 misc words (see the kernels)
     region = (region + 3) & ~3;
     P.region = region;
-    // shared addresses are kept as 16-bit values in the kernels: the block's
-    // dynamic shared memory plus the reserved 1 KB must stay below 64 KB
-    if ((long)(v.block_threads / G) * region * 4 + 1024 > 65535) return false;
+    // check edges are kept as 16-bit values in the kernels: byte addresses
+    // below 64 KB (the block's dynamic shared memory plus the reserved 1 KB),
+    // or, in the wide form, word indices of the group's region
+    if (wide_slots(G, v.pv_max, v.cv_max)) {
+        if (region > 65535 || (long)(v.block_threads / G) * region * 4 > 227 * 1024) return false;
+    } else if ((long)(v.block_threads / G) * region * 4 + 1024 > 65535) {
+        return false;
+    }
     // variable placement and edge order (bpdc_layout.cu)
     const int npos = P.pv * G;
     Layout lay;
@@ -261,7 +266,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
 {
     // automatic preference: one warp per shot for small graphs, then the
     // 256- and 512-thread groups
-    static const int kOrder[] = {0, 12, 5, 11, 1, 3, 2, 4, 6};
+    static const int kOrder[] = {0, 12, 5, 11, 1, 3, 2, 4, 6, 13};
     Packed P{};
     int vid = -1;
     for (int id : kOrder) {

@@ -13,9 +13,13 @@ constexpr float kLlrCap = 1e30f;
 // Marks an unused check slot (row shorter than the kernel's maximum degree).
 constexpr uint16_t kNoEdge = 0xFFFF;
 // Limits of the compiled kernel variants.
-constexpr int kMaxRowWeight = 16;
-constexpr int kMaxColWeight = 8;
 constexpr int kMaxDRowWeight = 64;
+
+// Check edges are kept as 16-bit values in registers.  A group whose message
+// slots fit in 64 KB of shared memory keeps byte addresses in the block's
+// shared window; a larger group (one per block) keeps word indices into its
+// own region and scales them when it loads or stores.
+constexpr bool wide_slots(int G, int pv, int cv) { return (long)G * pv * cv * 4 > 60 * 1024; }
 
 // Device-resident decoding problem, laid out for a group of G threads per
 // shot.  Variable j sits at lane j % G, pass j / G; check i at lane i % G,

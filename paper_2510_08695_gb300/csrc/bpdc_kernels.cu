@@ -188,9 +188,12 @@ struct Lane {
     static constexpr int kVmWords = (PVM * CVM + 31) / 32;
 
     static constexpr int kAddrWords = (PCM * DCM + 1) / 2;
+    static constexpr bool kWide = wide_slots(G, PVM, CVM);
     // shared byte address of each check edge's slot (the +inf word if none),
-    // two 16-bit addresses per word (blocks use less than 64 KB of shared memory)
+    // two 16-bit values per word: the address itself when the block uses less
+    // than 64 KB of shared memory, else the word index in the group's region
     uint32_t aw[kAddrWords];
+    uint32_t region_base;      // shared byte address of the group's region (wide form)
     uint32_t vm[kVmWords];     // bit (p*CVM + m): the variable at pass p has an m-th edge
     uint32_t vvalid;           // bit p: a variable sits at pass p
     uint32_t cvalid;           // bit p: a check sits at pass p
@@ -207,7 +210,9 @@ struct Lane {
     __device__ __forceinline__ uint32_t addr(int p, int k) const
     {
         const int n = p * DCM + k;
-        return (n & 1) ? (aw[n >> 1] >> 16) : (aw[n >> 1] & 0xFFFFu);
+        const uint32_t h = (n & 1) ? (aw[n >> 1] >> 16) : (aw[n >> 1] & 0xFFFFu);
+        if constexpr (kWide) return region_base + 4u * h;
+        return h;
     }
 
     __device__ void reload_lam(const DevGraph &g, int u)
@@ -224,6 +229,7 @@ struct Lane {
     {
         lane_base = slot_base + 4u * (uint32_t)u;
         inf_addr = inf_word;
+        region_base = slot_base - 4u * kMiscWords;
         cvalid = 0;
 #pragma unroll
         for (int w = 0; w < kAddrWords; ++w) aw[w] = 0;
@@ -234,7 +240,9 @@ struct Lane {
             for (int k = 0; k < DCM; ++k) {
                 uint32_t v = kNoEdge;
                 if (p < g.pc && k < g.dc) v = __ldg(g.chk_idx + ((size_t)p * g.dc + k) * G + u);
-                const uint32_t a = ((v == kNoEdge) ? inf_word : slot_base + 4u * v) & 0xFFFFu;
+                uint32_t a;
+                if constexpr (kWide) a = (v == kNoEdge) ? 2u : (uint32_t)kMiscWords + v;   // region words
+                else a = ((v == kNoEdge) ? inf_word : slot_base + 4u * v) & 0xFFFFu;
                 const int n = p * DCM + k;
                 aw[n >> 1] |= a << ((n & 1) * 16);
             }
@@ -307,7 +315,12 @@ struct Decoder {
             for (int p = 0; p < PCM; ++p) {
                 if (p < g.pc) {
                     const bool live = (ln.cvalid >> p) & 1u;
-                    uint32_t qb[DCM];
+                    // rows of up to 16 edges keep the gathered q in registers for
+                    // the scatter; longer rows read each q again before
+                    // overwriting it (one more load per edge, no register array)
+                    constexpr bool kHold = DCM <= 16;
+                    static_assert(kHold || RULE == 0, "product-sum rows are limited to 16 edges");
+                    uint32_t qb[kHold ? DCM : 1];
                     uint32_t S = ((sbits >> p) & 1u) ? 0x80000001u : 0u;
                     if constexpr (RULE == 0) {
                         // normalized min-sum
@@ -316,7 +329,7 @@ struct Decoder {
                         for (int k = 0; k < DCM; ++k) {
                             // unused slots point at the group's +inf word
                             const uint32_t b = lds32(ln.addr(p, k));
-                            qb[k] = b;
+                            if constexpr (kHold) qb[k] = b;
                             S ^= b;   // bit 31: sign parity, bit 0: hard-decision parity
                             const float av = fabsf(__uint_as_float(b));
                             mn2 = fminf(mn2, fmaxf(mn1, av));
@@ -334,8 +347,11 @@ struct Decoder {
 #pragma unroll
                             for (int k = 0; k < DCM; ++k) {
                                 const uint32_t a = ln.addr(p, k);
-                                const bool is_min = fabsf(__uint_as_float(qb[k])) == mn1;
-                                const uint32_t out = (is_min ? m2 : m1) ^ (qb[k] & 0x80000000u);
+                                uint32_t qk;
+                                if constexpr (kHold) qk = qb[k];
+                                else qk = lds32(a);
+                                const bool is_min = fabsf(__uint_as_float(qk)) == mn1;
+                                const uint32_t out = (is_min ? m2 : m1) ^ (qk & 0x80000000u);
                                 if (RC) sts32(a, out);
                                 else sts32_if(a, out, a != ln.inf_addr);
                             }
@@ -736,13 +752,11 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Variant table: (id, G, checks passes, row weight, variable passes, slots per
-// variable, block threads).
-// (id, G, check passes, row weight, variable passes, column weight, regular
-// columns, regular rows, block threads, min blocks per SM)
-// (id, G, check passes, row weight, variable passes, column weight, minimum
-// column weight, regular rows, check rule (0 min-sum, 1 product-sum), block
-// threads, min blocks per SM)
+// Variant table: (id, G, check passes, row weight, variable passes, column
+// weight, minimum column weight, regular rows, check rule (0 min-sum,
+// 1 product-sum), block threads, min blocks per SM).  Variant 13 takes
+// circuit-level detector models (rows of up to 35 edges, ~217 KB of message
+// slots per shot, one shot per SM).
 #define BPDC_VARIANTS(X)                               \
     X(0, 32, 3, 6, 5, 3, 3, true, 0, 256, 4)           \
     X(1, 256, 5, 7, 10, 4, 3, true, 0, 256, 3)         \
@@ -756,7 +770,8 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
     X(9, 512, 3, 7, 5, 4, 3, true, 0, 512, 1)          \
     X(10, 256, 4, 8, 11, 3, 2, false, 0, 256, 2)       \
     X(11, 32, 4, 4, 4, 2, 1, false, 1, 256, 4)         \
-    X(12, 32, 3, 6, 5, 3, 3, true, 1, 256, 4)
+    X(12, 32, 3, 6, 5, 3, 3, true, 1, 256, 4)          \
+    X(13, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1)
 
 static const Variant kVariants[] = {
 #define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB) {id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB},

@@ -71,13 +71,21 @@ cudaError_t measure_smem_peak(int reps, double *bytes_per_s, double *bytes_per_s
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int grid = 2 * sms;   // two 1024-thread blocks per SM: one full wave
+    const int smem = kPeakWords * 4;
+    e = cudaFuncSetAttribute((const void *)smem_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)smem_peak_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smem_peak_kernel, kPeakThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = per_sm * sms;   // one full wave: every block of an SM runs concurrently
     uint32_t *sink = nullptr;
     long long *cyc = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
-    const int smem = kPeakWords * 4;
-    e = cudaFuncSetAttribute((const void *)smem_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(uint32_t));
+    e = cudaMalloc(&sink, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&cyc, sizeof(long long) * grid);
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
@@ -103,8 +111,8 @@ cudaError_t measure_smem_peak(int reps, double *bytes_per_s, double *bytes_per_s
         const double bps = bytes / (ms * 1e-3);
         if (bps > best_bps) {
             best_bps = bps;
-            // all blocks run concurrently (one wave), so the SMs moved
-            // `bytes` in `mean_cyc` of their own clock cycles
+            // all blocks of an SM run concurrently (one wave), so each SM moved
+            // per_sm blocks' bytes in about `mean_cyc` of its own clock cycles
             best_bpc = bytes / (mean_cyc * sms);
             best_hz = mean_cyc / (ms * 1e-3);
         }

@@ -342,3 +342,48 @@ def test_smem_peak_microbenchmark(pkg):
     assert m["num_sms"] == torch.cuda.get_device_properties(0).multi_processor_count
     assert 64.0 < m["bytes_per_sm_clock"] <= 128.5, m
     assert 0.5e9 < m["sm_clock_hz"] < 3.0e9, m
+
+
+# ---------------------------------------------------------------------------
+# circuit-level detector error models (Appendix C / D; kernel 13)
+
+def test_circuit_level_parity_bb72(pkg, oracle_mod):
+    """BB[[72,12,6]], 6 noisy rounds, p = 2e-3: H_DCM 252 x 2232 with rows of
+    up to 35 edges, H_DDM for w = 3, T_iter = 1000 (Sec. IV), priors p for
+    the second BP."""
+    from bpdc_inputs import circuit
+    P = circuit.circuit_level_problem("bb72", 6, 2e-3)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 400, dict(ms_scale=0.625, max_iter=1000))
+    assert g.info["kernel_id"] == 13
+    rep = _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.6)
+    assert rep["status_ref"][1] > 20
+
+
+def test_circuit_level_parity_bb144_full_size(pkg, oracle_mod):
+    """The circuit-level serving model at full size: BB[[144,12,12]], 12
+    rounds, p = 1e-3 (H_DCM 936 x 8784), on a sample of shots at global
+    offsets spread over a 10^6-shot range, in the launch the server uses."""
+    from bpdc_inputs import circuit
+    P = circuit.circuit_level_problem("bb144", 12, 1e-3)
+    opts = pkg.Options(ms_scale=0.625, max_iter=1000)
+    g = pkg.Graph.from_problem(P, opts)
+    assert g.info["kernel_id"] == 13
+    offs = [0, 333_333, 999_900]
+    s = np.concatenate([sample_shots(P, SEED + 20, off, 50)[1] for off in offs])
+    o = np.concatenate([sample_shots(P, SEED + 20, off, 50)[2] for off in offs])
+    items = [dict(graph=g, syndromes=to_dev(s[i * 50:(i + 1) * 50]), shot_offset=off,
+                  obs_true=to_dev(o[i * 50:(i + 1) * 50]), out=g.alloc_outputs(50))
+             for i, off in enumerate(offs)]
+    pkg.decode_multi(items)      # one persistent launch over the three batches
+    g.sync_status()
+    import torch
+    out = {k: torch.cat([it["out"][k] for it in items]) for k in items[0]["out"]}
+    oo = oracle_mod.Options(alpha=0.625, max_iter=1000)
+    refs = [oracle_mod.decode_batch(P, s[i * 50:(i + 1) * 50], off, oo, want_post=True, want_post1=True)
+            for i, off in enumerate(offs)]
+    ref = {k: np.concatenate([r[k] for r in refs]) for k in refs[0]}
+    wc = [well_conditioned(oracle_mod, P, s[i * 50:(i + 1) * 50], off, oo, refs[i], draws=1)
+          for i, off in enumerate(offs)]
+    ref["well_conditioned"] = np.concatenate(wc)
+    rep = _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.5)
+    assert rep["status_ref"][1] > 10
