@@ -321,15 +321,16 @@ def main():
     dom = max(per_variant, key=lambda v: v["ms"])
     sm_mhz = clk.get("sm_mhz") or 2070.0
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    bpc = smem_peak.get("bytes_per_sm_clock")
-    if bpc:
-        peak_src = (f"measured: shared-memory microbenchmark {bpc:.1f} B per SM clock (nominal "
-                    f"{SMEM_BYTES_PER_CLK_PER_SM}) x {nsm} SMs x median sampled SM clock {sm_mhz:.0f} MHz")
+    nominal_gbs = nsm * SMEM_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9
+    if smem_peak.get("bytes_per_s"):
+        peak_gbs = smem_peak["bytes_per_s"] / 1e9
+        peak_src = (f"measured: shared-memory microbenchmark (bpdc_measure_smem_peak) before the timed region, "
+                    f"{peak_gbs / nominal_gbs:.3f} of the nominal {nsm} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk "
+                    f"x median sampled SM clock {sm_mhz:.0f} MHz = {nominal_gbs:.0f} GB/s")
     else:
-        bpc = SMEM_BYTES_PER_CLK_PER_SM
+        peak_gbs = nominal_gbs
         peak_src = (f"nominal: {nsm} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x median sampled SM clock "
                     f"{sm_mhz:.0f} MHz (microbenchmark failed)")
-    peak_gbs = nsm * bpc * sm_mhz * 1e6 / 1e9
     achieved_gbs = dom["edge_updates"] * EDGE_UPDATE_BYTES / (dom["ms"] / 1e3) / 1e9
     total_eu = sum(v["edge_updates"] for v in per_variant)
     traffic, smem_traffic, prof_file = profiled_traffic(dom["kernel_id"], dom["shots"], dom["edge_updates"])

@@ -243,14 +243,12 @@ int bpdc_graph_sync_status(bpdc_graph_t g, void *stream);
  * per message per phase).  Runs a microbenchmark of conflict-free 4-byte
  * loads and stores (8 + 8 per thread and iteration, `reps` iterations,
  * reps >= 8, one wave of as many 1024-thread blocks per SM as fit with 64 KB
- * of shared memory each, about 0.5 us per iteration)
- * three times after a warm-up run and reports the best: bytes moved per
- * second (CUDA events around the launch), bytes per SM clock cycle (from the
- * blocks' own cycle counters) and the SM clock those imply, plus the number
- * of SMs.  Synchronous; allocates and frees a few bytes of device memory.
+ * of shared memory each, about 0.5 us per iteration at 2 GHz) three times
+ * after a warm-up run and reports the best rate in bytes per second (CUDA
+ * events around the launch; at whatever SM clock the GPU runs then) and the
+ * number of SMs.  Synchronous; allocates and frees 4 bytes of device memory.
  * Errors: BPDC_ERR_INVALID_ARG (NULL output, reps < 8), BPDC_ERR_CUDA. */
-int bpdc_measure_smem_peak(int32_t device, int32_t reps, double *bytes_per_second,
-                           double *bytes_per_sm_clock, double *sm_clock_hz, int32_t *num_sms);
+int bpdc_measure_smem_peak(int32_t device, int32_t reps, double *bytes_per_second, int32_t *num_sms);
 
 /* Gradient of a weighted-BP loss (differentiable weighted BP).  Not
  * implemented: always returns BPDC_ERR_UNSUPPORTED. */

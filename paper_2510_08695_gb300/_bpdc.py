@@ -108,8 +108,8 @@ def load(build_if_missing: bool = True):
         "bpdc_sample": (ctypes.c_int, [vp, i64, u64, u64, vp, vp, vp, vp]),
         "bpdc_graph_sync_status": (ctypes.c_int, [vp, vp]),
         "bpdc_decode_backward": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, vp]),
-        "bpdc_measure_smem_peak": (ctypes.c_int, [i32, i32] + [ctypes.POINTER(ctypes.c_double)] * 3 +
-                                   [ctypes.POINTER(ctypes.c_int32)]),
+        "bpdc_measure_smem_peak": (ctypes.c_int, [i32, i32, ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_int32)]),
         "bpdc_last_error": (ctypes.c_char_p, []),
         "bpdc_version": (ctypes.c_char_p, []),
     }
@@ -339,11 +339,10 @@ def layout_plan(H, G: int, optimize: bool = True):
 def measure_smem_peak(device: int = 0, reps: int = 40000) -> dict:
     """Shared-memory bandwidth microbenchmark (bpdc_measure_smem_peak)."""
     lib = load()
-    bps, bpc, hz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    bps = ctypes.c_double()
     sms = ctypes.c_int32()
-    _check(lib.bpdc_measure_smem_peak(int(device), int(reps), ctypes.byref(bps), ctypes.byref(bpc),
-                                      ctypes.byref(hz), ctypes.byref(sms)))
-    return dict(bytes_per_s=bps.value, bytes_per_sm_clock=bpc.value, sm_clock_hz=hz.value, num_sms=sms.value)
+    _check(lib.bpdc_measure_smem_peak(int(device), int(reps), ctypes.byref(bps), ctypes.byref(sms)))
+    return dict(bytes_per_s=bps.value, num_sms=sms.value)
 
 
 def version() -> str:

@@ -774,15 +774,14 @@ int bpdc_graph_sync_status(bpdc_graph_t g, void *stream)
     return BPDC_OK;
 }
 
-int bpdc_measure_smem_peak(int32_t device, int32_t reps, double *bytes_per_second,
-                           double *bytes_per_sm_clock, double *sm_clock_hz, int32_t *num_sms)
+int bpdc_measure_smem_peak(int32_t device, int32_t reps, double *bytes_per_second, int32_t *num_sms)
 {
-    if (!bytes_per_second || !bytes_per_sm_clock || !sm_clock_hz || !num_sms || reps < 8)
+    if (!bytes_per_second || !num_sms || reps < 8)
         return fail(BPDC_ERR_INVALID_ARG, "bpdc_measure_smem_peak: NULL output or reps < 8");
     DeviceGuard dgd(device);
     if (!dgd.ok) return fail(BPDC_ERR_CUDA, "cannot select device %d", device);
     int sms = 0;
-    cudaError_t e = measure_smem_peak(reps, bytes_per_second, bytes_per_sm_clock, sm_clock_hz, &sms);
+    cudaError_t e = measure_smem_peak(reps, bytes_per_second, &sms);
     if (e != cudaSuccess) return cuda_fail(e, "shared-memory microbenchmark");
     *num_sms = sms;
     return BPDC_OK;

@@ -123,8 +123,7 @@ cudaError_t launch_cut_select(const DevGraph &g, int64_t B, const float *post, u
                               uint32_t *cut_out, cudaStream_t s);
 // Shared-memory bandwidth microbenchmark (bpdc_peak.cu): best of three timed
 // runs of `reps` iterations on the current device.
-cudaError_t measure_smem_peak(int reps, double *bytes_per_s, double *bytes_per_sm_clock, double *sm_hz,
-                              int *num_sms);
+cudaError_t measure_smem_peak(int reps, double *bytes_per_s, int *num_sms);
 cudaError_t launch_sample(const DevGraph &g, int64_t B, uint64_t seed, uint64_t shot_offset,
                           uint32_t *syn, uint32_t *obs, uint32_t *err, cudaStream_t s);
 

@@ -5,13 +5,10 @@
 // Every thread streams 4-byte loads and stores over a conflict-free 64 KB
 // tile (lane-consecutive words, like the variable-major message slots), so
 // each warp-wide access is one 128-byte wavefront.  Blocks fill every SM in
-// one wave; each block also records its SM-clock cycle count so that the
-// host can express the result per SM clock, independent of the clock the
-// GPU happened to run at.
+// one wave; CUDA events around the launch give the bytes moved per second.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <vector>
 
 #include "bpdc_internal.h"
 
@@ -21,14 +18,12 @@ namespace {
 constexpr int kPeakThreads = 1024;
 constexpr int kPeakWords = 16 * kPeakThreads;   // 64 KB per block
 
-__global__ void __launch_bounds__(kPeakThreads, 2) smem_peak_kernel(int reps, uint32_t *sink,
-                                                                    long long *cycles)
+__global__ void __launch_bounds__(kPeakThreads, 2) smem_peak_kernel(int reps, uint32_t *sink)
 {
     extern __shared__ uint32_t tile[];   // kPeakWords words
     const uint32_t base = (uint32_t)__cvta_generic_to_shared(tile) + 4u * threadIdx.x;
     for (int i = threadIdx.x; i < kPeakWords; i += blockDim.x) tile[i] = i;
     __syncthreads();
-    const long long t0 = clock64();
     uint32_t acc = threadIdx.x;
     for (int r = 0; r < reps; ++r) {
         uint32_t v0, v1, v2, v3, v4, v5, v6, v7;
@@ -56,16 +51,12 @@ __global__ void __launch_bounds__(kPeakThreads, 2) smem_peak_kernel(int reps, ui
             ::"r"(base), "r"(acc), "r"(v0), "r"(v1), "r"(v2), "r"(v3), "r"(v4), "r"(v5), "r"(v6)
             : "memory");
     }
-    __syncthreads();
-    const long long t1 = clock64();
     if (acc == 0x9E3779B9u) sink[0] = acc;   // keeps the loop observable
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
 }  // namespace
 
-cudaError_t measure_smem_peak(int reps, double *bytes_per_s, double *bytes_per_sm_clock, double *sm_hz,
-                              int *num_sms)
+cudaError_t measure_smem_peak(int reps, double *bytes_per_s, int *num_sms)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -83,48 +74,32 @@ cudaError_t measure_smem_peak(int reps, double *bytes_per_s, double *bytes_per_s
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int grid = per_sm * sms;   // one full wave: every block of an SM runs concurrently
     uint32_t *sink = nullptr;
-    long long *cyc = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
     e = cudaMalloc(&sink, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&cyc, sizeof(long long) * grid);
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    double best_bps = 0.0, best_bpc = 0.0, best_hz = 0.0;
-    std::vector<long long> hc(grid);
+    double best_bps = 0.0;
     for (int trial = 0; e == cudaSuccess && trial < 4; ++trial) {
         const int r = trial == 0 ? reps / 8 : reps;   // the first run warms up
         e = cudaEventRecord(a, 0);
         if (e == cudaSuccess) {
-            smem_peak_kernel<<<grid, kPeakThreads, smem>>>(r, sink, cyc);
+            smem_peak_kernel<<<grid, kPeakThreads, smem>>>(r, sink);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(b, 0);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, sizeof(long long) * grid, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess || trial == 0 || ms <= 0.0f) continue;
         const double bytes = 64.0 * kPeakThreads * (double)r * grid;   // 8 loads + 8 stores of 4 B
-        double mean_cyc = 0.0;
-        for (long long c : hc) mean_cyc += (double)c;
-        mean_cyc /= grid;
         const double bps = bytes / (ms * 1e-3);
-        if (bps > best_bps) {
-            best_bps = bps;
-            // all blocks of an SM run concurrently (one wave), so each SM moved
-            // per_sm blocks' bytes in about `mean_cyc` of its own clock cycles
-            best_bpc = bytes / (mean_cyc * sms);
-            best_hz = mean_cyc / (ms * 1e-3);
-        }
+        if (bps > best_bps) best_bps = bps;
     }
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     if (sink) cudaFree(sink);
-    if (cyc) cudaFree(cyc);
     if (e != cudaSuccess) return e;
     *bytes_per_s = best_bps;
-    *bytes_per_sm_clock = best_bpc;
-    *sm_hz = best_hz;
     *num_sms = sms;
     return cudaSuccess;
 }

@@ -117,7 +117,5 @@ def test_valid_problem_needs_a_device_or_succeeds(lib):
 def test_smem_peak_rejects_bad_arguments(lib):
     d = ctypes.c_double()
     n = ctypes.c_int32()
-    assert lib.bpdc_measure_smem_peak(0, 100, None, ctypes.byref(d), ctypes.byref(d), ctypes.byref(n)) \
-        == _bpdc.ERR_INVALID_ARG
-    assert lib.bpdc_measure_smem_peak(0, 4, ctypes.byref(d), ctypes.byref(d), ctypes.byref(d),
-                                      ctypes.byref(n)) == _bpdc.ERR_INVALID_ARG
+    assert lib.bpdc_measure_smem_peak(0, 100, None, ctypes.byref(n)) == _bpdc.ERR_INVALID_ARG
+    assert lib.bpdc_measure_smem_peak(0, 4, ctypes.byref(d), ctypes.byref(n)) == _bpdc.ERR_INVALID_ARG
