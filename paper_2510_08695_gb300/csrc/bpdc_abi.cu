@@ -180,7 +180,7 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     // below 64 KB (the block's dynamic shared memory plus the reserved 1 KB),
     // or, in the wide form, word indices of the group's region
     if (wide_slots(G, v.pv_max, v.cv_max)) {
-        if (region > 65535 || (long)(v.block_threads / G) * region * 4 > 227 * 1024) return false;
+        if (region > 65535 || (long)(v.block_threads / G) * region * 4 > kMaxSmemPerBlock) return false;
     } else if ((long)(v.block_threads / G) * region * 4 + 1024 > 65535) {
         return false;
     }

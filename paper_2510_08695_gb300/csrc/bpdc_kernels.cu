@@ -51,11 +51,6 @@ namespace {
 
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 
-__device__ __forceinline__ float tag(float q, uint32_t e)
-{
-    return __uint_as_float((__float_as_uint(q) & ~1u) | e);
-}
-
 // SplitMix64 output number ctr of the stream keyed by key (Steele, Lea &
 // Flood 2014).
 __device__ __forceinline__ uint64_t splitmix64(uint64_t key, uint64_t ctr)
