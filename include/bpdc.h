@@ -39,6 +39,7 @@
 #ifndef BPDC_H
 #define BPDC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -250,11 +251,45 @@ int bpdc_graph_sync_status(bpdc_graph_t g, void *stream);
  * Errors: BPDC_ERR_INVALID_ARG (NULL output, reps < 8), BPDC_ERR_CUDA. */
 int bpdc_measure_smem_peak(int32_t device, int32_t reps, double *bytes_per_second, int32_t *num_sms);
 
-/* Gradient of a weighted-BP loss (differentiable weighted BP).  Not
- * implemented: always returns BPDC_ERR_UNSUPPORTED. */
-int bpdc_decode_backward(bpdc_graph_t g, int64_t B, const uint32_t *syndromes,
-                         const float *weights, const float *grad_llr, float *grad_weights,
-                         void *stream);
+/* ---- Weighted BP (differentiable decoding; not part of the paper) ------------
+ *
+ * Product-sum BP (the check rule Sec. II.C.1 cites) with one weight per edge,
+ * iteration and direction, unrolled for exactly T iterations (no early stop,
+ * no degeneracy cutting).  Edges e = (i, j) of H are numbered in CSR order
+ * (row by row, ascending column).  weights is device float [2][T][E]:
+ * W[0][t][e] = wc scales the check-to-variable message, W[1][t][e] = wv the
+ * variable-to-check message.  For t = 0..T-1:
+ *   q_e(t) = clip(wv[t][e] (lambda_j + sum_{e' in M(j), e' != e} r_e'(t-1)), -clip, clip),  r(-1) = 0
+ *   r_e(t) = wc[t][e] (-1)^{s_i} prod_{e' in N(i), e' != e} sgn(q_e'(t))
+ *            phi(sum_{e' in N(i), e' != e} phi(max(|q_e'(t)|, 1e-6))),   phi(x) = -log tanh(x/2)
+ *   L_j(t) = lambda_j + sum_{e in M(j)} r_e(t)
+ * Unit weights and a large clip give the decoder's product-sum BP.  Graphs
+ * need row weights 2..16 and column weights <= 8.  The forward keeps the q of
+ * iterations 0, k, 2k, ... (k = ckpt_every) in the caller's workspace; the
+ * backward recomputes each k-iteration segment from them, so both calls must
+ * get the same workspace, weights, syndromes, T, clip and ckpt_every, with the
+ * forward first.  Calls are stream-ordered and asynchronous.  Errors:
+ * BPDC_ERR_INVALID_ARG (NULL buffers, T outside [1, 1000], ckpt_every
+ * outside [1, T], clip outside (0, 30], workspace too small),
+ * BPDC_ERR_UNSUPPORTED (row/column weights, or more edges than the adjoint's
+ * shared memory holds), BPDC_ERR_CUDA. */
+
+/* Bytes of workspace the two calls need for B shots. */
+int bpdc_wbp_workspace_size(bpdc_graph_t g, int64_t B, int32_t T, int32_t ckpt_every, size_t *bytes);
+
+/* Forward: posterior LLRs of every iteration, device float [B][T][N] (may be
+ * NULL when only the checkpoints are wanted).  syndromes: device uint32
+ * [B][ceil(M/32)] as for bpdc_decode. */
+int bpdc_wbp_forward(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, const float *weights, int32_t T,
+                     float clip, int32_t ckpt_every, float *posteriors, void *workspace, size_t workspace_bytes,
+                     void *stream);
+
+/* Adjoint: given dLoss/dL_j(t) (device float [B][T][N]), writes
+ * dLoss/dW (device float [2][T][E], summed over the B shots in a fixed
+ * order, so the result is deterministic). */
+int bpdc_decode_backward(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, const float *weights, int32_t T,
+                         float clip, int32_t ckpt_every, const float *grad_posteriors, float *grad_weights,
+                         void *workspace, size_t workspace_bytes, void *stream);
 
 /* Message of the last error raised on the calling thread ("" if none). */
 const char *bpdc_last_error(void);

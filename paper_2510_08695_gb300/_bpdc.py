@@ -107,7 +107,11 @@ def load(build_if_missing: bool = True):
         "bpdc_cut_select": (ctypes.c_int, [vp, i64, vp, u64, vp, vp]),
         "bpdc_sample": (ctypes.c_int, [vp, i64, u64, u64, vp, vp, vp, vp]),
         "bpdc_graph_sync_status": (ctypes.c_int, [vp, vp]),
-        "bpdc_decode_backward": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, vp]),
+        "bpdc_wbp_workspace_size": (ctypes.c_int, [vp, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]),
+        "bpdc_wbp_forward": (ctypes.c_int, [vp, i64, vp, vp, i32, ctypes.c_float, i32, vp, vp, ctypes.c_size_t,
+                                            vp]),
+        "bpdc_decode_backward": (ctypes.c_int, [vp, i64, vp, vp, i32, ctypes.c_float, i32, vp, vp, vp,
+                                                ctypes.c_size_t, vp]),
         "bpdc_measure_smem_peak": (ctypes.c_int, [i32, i32, ctypes.POINTER(ctypes.c_double),
                                                   ctypes.POINTER(ctypes.c_int32)]),
         "bpdc_last_error": (ctypes.c_char_p, []),
@@ -320,9 +324,38 @@ def decode_multi_noalloc(items, stream=None):
     _check(lib.bpdc_decode_multi_noalloc(_batches(items), len(items), _stream_ptr(stream)))
 
 
-def decode_backward(graph: Graph, *args, **kw):
-    lib = load()
-    _check(lib.bpdc_decode_backward(graph.handle, 0, None, None, None, None, None))
+def wbp_workspace(graph: Graph, B: int, T: int, ckpt_every: int):
+    """A device workspace (uint8 tensor) for bpdc_wbp_forward / bpdc_decode_backward."""
+    import torch
+    n = ctypes.c_size_t()
+    _check(load().bpdc_wbp_workspace_size(graph.handle, int(B), int(T), int(ckpt_every), ctypes.byref(n)))
+    return torch.empty(max(int(n.value), 1), dtype=torch.uint8, device=torch.device("cuda", graph.device))
+
+
+def wbp_forward(graph: Graph, syndromes, weights, T: int, clip: float, ckpt_every: int, workspace,
+                posteriors=None, stream=None):
+    """bpdc_wbp_forward: posteriors [B, T, N] float32 of weighted BP."""
+    import torch
+    B = int(syndromes.shape[0])
+    if posteriors is None:
+        posteriors = torch.empty((B, T, graph.N), dtype=torch.float32, device=syndromes.device)
+    _check(load().bpdc_wbp_forward(graph.handle, B, _ptr(syndromes), _ptr(weights), int(T), float(clip),
+                                   int(ckpt_every), _ptr(posteriors), _ptr(workspace), workspace.numel(),
+                                   _stream_ptr(stream)))
+    return posteriors
+
+
+def decode_backward(graph: Graph, syndromes, weights, T: int, clip: float, ckpt_every: int, grad_posteriors,
+                    workspace, grad_weights=None, stream=None):
+    """bpdc_decode_backward: dLoss/dW [2, T, E] from dLoss/dL [B, T, N]."""
+    import torch
+    B = int(syndromes.shape[0])
+    if grad_weights is None:
+        grad_weights = torch.empty_like(weights)
+    _check(load().bpdc_decode_backward(graph.handle, B, _ptr(syndromes), _ptr(weights), int(T), float(clip),
+                                       int(ckpt_every), _ptr(grad_posteriors), _ptr(grad_weights),
+                                       _ptr(workspace), workspace.numel(), _stream_ptr(stream)))
+    return grad_weights
 
 
 def layout_plan(H, G: int, optimize: bool = True):

@@ -298,6 +298,19 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     const size_t o_dptr = put(blob, P.d_ptr), o_dent = put(blob, P.d_ent), o_l = put(blob, P.l_pos);
     const size_t o_dcol = put(blob, P.d_col), o_lcol = put(blob, P.l_cols), o_pcol = put(blob, P.pos_col);
     const size_t o_hptr = put(blob, g->H.ptr), o_hcol = put(blob, g->H.col), o_thr = put(blob, P.thr);
+    // column view of H and priors by column (weighted BP)
+    std::vector<int32_t> cptr(g->H.cols + 1, 0), cedge(g->H.col.size());
+    std::vector<float> lamc(g->H.cols);
+    for (int32_t c : g->H.col) cptr[c + 1]++;
+    for (int j = 0; j < g->H.cols; ++j) cptr[j + 1] += cptr[j];
+    {
+        std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+        for (int i = 0; i < g->H.rows; ++i)
+            for (int a = g->H.ptr[i]; a < g->H.ptr[i + 1]; ++a) cedge[fill[g->H.col[a]]++] = a;
+        for (int j = 0; j < g->H.cols; ++j)
+            lamc[j] = (float)std::log((1.0 - g->priors[j]) / g->priors[j]);
+    }
+    const size_t o_cptr = put(blob, cptr), o_cedge = put(blob, cedge), o_lamc = put(blob, lamc);
     const size_t o_err = put(blob, std::vector<int32_t>(4, 0));
     void *arena = nullptr;
     e = cudaMalloc(&arena, blob.size());
@@ -333,6 +346,9 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     d.h_ptr = (const int32_t *)(base + o_hptr);
     d.h_col = (const int32_t *)(base + o_hcol);
     d.thr = (const uint32_t *)(base + o_thr);
+    d.c_ptr = (const int32_t *)(base + o_cptr);
+    d.c_edge = (const int32_t *)(base + o_cedge);
+    d.lam_col = (const float *)(base + o_lamc);
     d.err_flag = (int32_t *)(base + o_err);
     g->variant = vid;
     g->groups_per_block = gpb;
@@ -787,10 +803,79 @@ int bpdc_measure_smem_peak(int32_t device, int32_t reps, double *bytes_per_secon
     return BPDC_OK;
 }
 
-int bpdc_decode_backward(bpdc_graph_t, int64_t, const uint32_t *, const float *, const float *, float *,
-                         void *)
+// Shared checks of the weighted-BP calls; fills the kernel arguments.
+static int wbp_prepare(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, const float *weights, int32_t T,
+                       float clip, int32_t ckpt_every, void *workspace, size_t workspace_bytes, WbpArgs &a)
 {
-    return fail(BPDC_ERR_UNSUPPORTED, "bpdc_decode_backward: differentiable weighted BP is not implemented");
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    if (B < 0) return fail(BPDC_ERR_INVALID_ARG, "B < 0");
+    if (T < 1 || T > 1000) return fail(BPDC_ERR_INVALID_ARG, "T must be in [1, 1000]");
+    if (ckpt_every < 1 || ckpt_every > T) return fail(BPDC_ERR_INVALID_ARG, "ckpt_every must be in [1, T]");
+    if (!(clip > 0.0f) || clip > 30.0f) return fail(BPDC_ERR_INVALID_ARG, "clip must be in (0, 30]");
+    if (B > 0 && (!syndromes || !weights)) return fail(BPDC_ERR_INVALID_ARG, "NULL syndromes or weights");
+    int rmin = 1 << 30, rmax = 0, cmax = 0;
+    std::vector<int> deg(g->H.cols, 0);
+    for (int i = 0; i < g->H.rows; ++i) {
+        const int d = g->H.ptr[i + 1] - g->H.ptr[i];
+        rmin = std::min(rmin, d);
+        rmax = std::max(rmax, d);
+    }
+    for (int32_t c : g->H.col) cmax = std::max(cmax, ++deg[c]);
+    if (rmin < 2 || rmax > kWbpMaxRow || cmax > kWbpMaxCol)
+        return fail(BPDC_ERR_UNSUPPORTED, "weighted BP needs row weights in [2, %d] and column weights <= %d",
+                    kWbpMaxRow, kWbpMaxCol);
+    const int E = (int)g->H.col.size();
+    if (wbp_smem_backward(E, ckpt_every, 1) > kMaxWbpSmem)
+        return fail(BPDC_ERR_UNSUPPORTED, "graph too large for the weighted-BP adjoint (%d edges)", E);
+    size_t need = 0;
+    bpdc_wbp_workspace_size(g, B, T, ckpt_every, &need);
+    if (B > 0 && (!workspace || workspace_bytes < need))
+        return fail(BPDC_ERR_INVALID_ARG, "workspace of %zu bytes needed", need);
+    const size_t nck = (size_t)B * ((T + ckpt_every - 1) / ckpt_every) * E;
+    a = WbpArgs{};
+    a.B = B; a.E = E; a.T = T; a.k = ckpt_every; a.clip = clip;
+    a.syn = syndromes; a.W = weights;
+    a.ckpt = (float *)workspace;
+    a.part = (float *)workspace + ((nck + 63) & ~(size_t)63);
+    return BPDC_OK;
+}
+
+int bpdc_wbp_workspace_size(bpdc_graph_t g, int64_t B, int32_t T, int32_t ckpt_every, size_t *bytes)
+{
+    if (!g || !bytes || B < 0 || T < 1 || ckpt_every < 1)
+        return fail(BPDC_ERR_INVALID_ARG, "bpdc_wbp_workspace_size: bad argument");
+    const size_t E = g->H.col.size();
+    const size_t nck = (size_t)B * ((T + ckpt_every - 1) / ckpt_every) * E;
+    *bytes = (((nck + 63) & ~(size_t)63) + (size_t)B * 2 * T * E) * sizeof(float);
+    return BPDC_OK;
+}
+
+int bpdc_wbp_forward(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, const float *weights, int32_t T,
+                     float clip, int32_t ckpt_every, float *posteriors, void *workspace, size_t workspace_bytes,
+                     void *stream)
+{
+    WbpArgs a;
+    int rc = wbp_prepare(g, B, syndromes, weights, T, clip, ckpt_every, workspace, workspace_bytes, a);
+    if (rc != BPDC_OK || B == 0) return rc;
+    a.post = posteriors;
+    DeviceGuard dgd(g->device);
+    cudaError_t e = launch_wbp_forward(g->dg, a, (cudaStream_t)stream);
+    return e == cudaSuccess ? BPDC_OK : cuda_fail(e, "weighted-BP forward launch");
+}
+
+int bpdc_decode_backward(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, const float *weights, int32_t T,
+                         float clip, int32_t ckpt_every, const float *grad_posteriors, float *grad_weights,
+                         void *workspace, size_t workspace_bytes, void *stream)
+{
+    WbpArgs a;
+    int rc = wbp_prepare(g, B, syndromes, weights, T, clip, ckpt_every, workspace, workspace_bytes, a);
+    if (rc != BPDC_OK) return rc;
+    if (!grad_weights || (B > 0 && !grad_posteriors))
+        return fail(BPDC_ERR_INVALID_ARG, "NULL gradient buffer");
+    a.gpost = grad_posteriors;
+    DeviceGuard dgd(g->device);
+    cudaError_t e = launch_wbp_backward(g->dg, a, grad_weights, (cudaStream_t)stream);
+    return e == cudaSuccess ? BPDC_OK : cuda_fail(e, "weighted-BP backward launch");
 }
 
 }  // extern "C"

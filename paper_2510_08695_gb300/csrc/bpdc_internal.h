@@ -54,6 +54,9 @@ struct DevGraph {
     const int32_t *h_ptr;        // [M+1] rows of H (sampler)
     const int32_t *h_col;        // [E]
     const uint32_t *thr;         // [N] floor(p * 2^32) (sampler)
+    const int32_t *c_ptr;        // [N+1] columns of H: edges of variable j are c_edge[c_ptr[j] .. c_ptr[j+1])
+    const int32_t *c_edge;       // [E] edge ids (CSR order of H) by column, ascending check
+    const float *lam_col;        // [N] prior LLR by column (weighted BP)
     int32_t *err_flag;           // latched device error code
 };
 
@@ -121,6 +124,28 @@ cudaError_t launch_variant_static(int id, const BatchDesc *host_descs, int n, in
 
 cudaError_t launch_cut_select(const DevGraph &g, int64_t B, const float *post, uint64_t shot_offset,
                               uint32_t *cut_out, cudaStream_t s);
+// Weighted product-sum BP (bpdc_wbp.cu).  Limits: row weight 2..16, column
+// weight <= 8; weights W[2][T][E] (E = edges of H in CSR order; W[0] check ->
+// variable, W[1] variable -> check).
+constexpr int kWbpMaxRow = 16;
+constexpr int kWbpMaxCol = 8;
+constexpr size_t kMaxWbpSmem = 227 * 1024;
+struct WbpArgs {
+    int64_t B;
+    int E, T, k;                 // edges, iterations, checkpoint interval
+    float clip;                  // |q| <= clip
+    const uint32_t *syn;         // [B][MW]
+    const float *W;              // [2][T][E]
+    float *post;                 // [B][T][N] or null
+    float *ckpt;                 // [B][ceil(T/k)][E] q of iterations 0, k, 2k, ...
+    const float *gpost;          // [B][T][N] adjoint of the posteriors (backward)
+    float *part;                 // [B][2][T][E] per-shot gradient partials (backward)
+};
+size_t wbp_smem_forward(int E, int warps);
+size_t wbp_smem_backward(int E, int k, int warps);
+cudaError_t launch_wbp_forward(const DevGraph &g, const WbpArgs &a, cudaStream_t s);
+cudaError_t launch_wbp_backward(const DevGraph &g, const WbpArgs &a, float *grad_w, cudaStream_t s);
+
 // Shared-memory bandwidth microbenchmark (bpdc_peak.cu): best of three timed
 // runs of `reps` iterations on the current device.
 cudaError_t measure_smem_peak(int reps, double *bytes_per_s, int *num_sms);

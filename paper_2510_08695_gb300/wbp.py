@@ -1,0 +1,74 @@
+"""Differentiable weighted BP on the GPU.
+
+``weighted_bp(weights, graph, syndromes)`` is a ``torch.autograd.Function``
+over the library's forward kernel (``bpdc_wbp_forward``) and hand-written
+adjoint (``bpdc_decode_backward``): posterior LLRs [B, T, N] of T unrolled
+product-sum iterations with per-edge, per-iteration weights [2, T, E]
+(definition in include/bpdc.h).  Messages are checkpointed every
+``ckpt_every`` iterations and recomputed per segment in the backward pass.
+
+``train_weights`` fits the weights on shots the library samples itself, with
+the binary cross-entropy of the posteriors against the sampled errors.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _bpdc
+
+
+class WeightedBP(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, weights, graph, syndromes, clip: float = 20.0, ckpt_every: int = 5):
+        T = int(weights.shape[1])
+        w = weights.detach().contiguous()
+        ws = _bpdc.wbp_workspace(graph, syndromes.shape[0], T, ckpt_every)
+        post = _bpdc.wbp_forward(graph, syndromes, w, T, clip, ckpt_every, ws)
+        ctx.save_for_backward(w)
+        ctx.graph, ctx.syn, ctx.ws, ctx.clip, ctx.k = graph, syndromes, ws, clip, ckpt_every
+        return post
+
+    @staticmethod
+    def backward(ctx, grad_post):
+        (w,) = ctx.saved_tensors
+        g = _bpdc.decode_backward(ctx.graph, ctx.syn, w, int(w.shape[1]), ctx.clip, ctx.k,
+                                  grad_post.contiguous(), ctx.ws)
+        return g, None, None, None, None
+
+
+def weighted_bp(weights, graph, syndromes, clip: float = 20.0, ckpt_every: int = 5):
+    return WeightedBP.apply(weights, graph, syndromes, clip, ckpt_every)
+
+
+def bce_loss(post, errors):
+    """Mean binary cross-entropy of sigma(-L) against the errors (float [B, N]),
+    over shots, iterations and variables."""
+    e = errors[:, None, :]
+    return (e * torch.nn.functional.softplus(post) + (1 - e) * torch.nn.functional.softplus(-post)).mean()
+
+
+def unpack_words(words, n: int):
+    """int32 bit words [B, ceil(n/32)] -> float32 {0, 1} [B, n] on the same device."""
+    w = words.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    bits = (w[:, :, None] >> torch.arange(32, device=w.device)) & 1
+    return bits.reshape(w.shape[0], -1)[:, :n].to(torch.float32)
+
+
+def train_weights(graph, T: int = 20, steps: int = 50, batch: int = 4096, lr: float = 0.01, seed: int = 11,
+                  clip: float = 20.0, ckpt_every: int = 5, weights=None):
+    """Adam on the BCE loss over freshly sampled batches (shot offsets advance
+    every step).  Returns (weights [2, T, E], list of losses)."""
+    dev = torch.device("cuda", graph.device)
+    W = (torch.ones((2, T, graph.E), dtype=torch.float32, device=dev) if weights is None
+         else weights.detach().clone()).requires_grad_(True)
+    opt = torch.optim.Adam([W], lr=lr)
+    hist = []
+    for s in range(steps):
+        syn, _, err = graph.sample(batch, seed, s * batch, errors=True)
+        post = weighted_bp(W, graph, syn, clip, ckpt_every)
+        loss = bce_loss(post, unpack_words(err, graph.N))
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        hist.append(float(loss.detach()))
+    return W.detach(), hist

@@ -99,8 +99,12 @@ def test_argument_validation(lib):
     assert lib.bpdc_graph_destroy(None) == 0
 
 
-def test_backward_reports_unsupported(lib):
-    assert lib.bpdc_decode_backward(None, 0, None, None, None, None, None) == _bpdc.ERR_UNSUPPORTED
+def test_weighted_bp_calls_reject_a_null_graph(lib):
+    n = ctypes.c_size_t()
+    assert lib.bpdc_wbp_workspace_size(None, 1, 20, 5, ctypes.byref(n)) == _bpdc.ERR_INVALID_ARG
+    assert lib.bpdc_wbp_forward(None, 1, None, None, 20, 20.0, 5, None, None, 0, None) == _bpdc.ERR_INVALID_ARG
+    assert lib.bpdc_decode_backward(None, 1, None, None, 20, 20.0, 5, None, None, None, 0, None) \
+        == _bpdc.ERR_INVALID_ARG
 
 
 def test_valid_problem_needs_a_device_or_succeeds(lib):
