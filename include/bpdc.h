@@ -274,6 +274,17 @@ int bpdc_measure_smem_peak(int32_t device, int32_t reps, double *bytes_per_secon
  * BPDC_ERR_UNSUPPORTED (row/column weights, or more edges than the adjoint's
  * shared memory holds), BPDC_ERR_CUDA. */
 
+/* Makes bpdc_decode / bpdc_decode_multi run weighted BP with learned weights
+ * (host float [2][T][E], the layout above; copied) inside BP+DC: decoding
+ * iteration t (t = 1, 2, ...) uses weight set min(t, T) - 1, both BP runs
+ * start from set 0, and variable-to-check messages are clipped to +-clip, so
+ * that the first T iterations of a run equal bpdc_wbp_forward's.  NULL
+ * weights restore plain BP.  The graph must use the product-sum rule
+ * (variant 1).  Errors: BPDC_ERR_INVALID_ARG (T outside [1, 1000], clip
+ * outside (0, 30], non-finite weight), BPDC_ERR_UNSUPPORTED (min-sum graph),
+ * BPDC_ERR_CUDA / BPDC_ERR_OOM (re-upload). */
+int bpdc_graph_set_weights(bpdc_graph_t g, const float *weights, int32_t T, float clip);
+
 /* Bytes of workspace the two calls need for B shots. */
 int bpdc_wbp_workspace_size(bpdc_graph_t g, int64_t B, int32_t T, int32_t ckpt_every, size_t *bytes);
 

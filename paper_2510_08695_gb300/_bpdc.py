@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
         "bpdc_cut_select": (ctypes.c_int, [vp, i64, vp, u64, vp, vp]),
         "bpdc_sample": (ctypes.c_int, [vp, i64, u64, u64, vp, vp, vp, vp]),
         "bpdc_graph_sync_status": (ctypes.c_int, [vp, vp]),
+        "bpdc_graph_set_weights": (ctypes.c_int, [vp, vp, i32, ctypes.c_float]),
         "bpdc_wbp_workspace_size": (ctypes.c_int, [vp, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]),
         "bpdc_wbp_forward": (ctypes.c_int, [vp, i64, vp, vp, i32, ctypes.c_float, i32, vp, vp, ctypes.c_size_t,
                                             vp]),
@@ -288,6 +289,19 @@ class Graph:
         _check(_lib.bpdc_sample(self.handle, int(B), ctypes.c_uint64(seed), ctypes.c_uint64(shot_offset),
                                 _ptr(syn), _ptr(obs), _ptr(err), _stream_ptr(stream)))
         return syn, obs, err
+
+    def set_weights(self, weights=None, clip: float = 20.0):
+        """Learned weighted-BP weights [2, T, E] (CPU or CUDA tensor, or numpy)
+        used by decode / decode_multi; None restores plain BP."""
+        if weights is None:
+            _check(_lib.bpdc_graph_set_weights(self.handle, None, 0, ctypes.c_float(0.0)))
+            return
+        w = np.ascontiguousarray(np.asarray(weights.detach().cpu() if hasattr(weights, "detach") else weights,
+                                            dtype=np.float32))
+        assert w.ndim == 3 and w.shape[0] == 2 and w.shape[2] == self.E, w.shape
+        _check(_lib.bpdc_graph_set_weights(self.handle, w.ctypes.data_as(ctypes.c_void_p), int(w.shape[1]),
+                                           ctypes.c_float(clip)))
+        self._refresh()
 
     def sync_status(self, stream=None):
         _check(_lib.bpdc_graph_sync_status(self.handle, _stream_ptr(stream)))

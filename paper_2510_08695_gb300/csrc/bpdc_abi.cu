@@ -118,6 +118,9 @@ struct bpdc_graph_s {
     RingSlot ring[kRing];
     int ring_next = 0;
     int layout = 1;   // 1: bank-conflict-aware placement, 0: identity
+    std::vector<float> w_host;   // learned weights [2][w_T][E] (CSR edge order), empty if none
+    int w_T = 0;
+    float w_clip = 0.0f;
     std::mutex mu;
 };
 
@@ -137,6 +140,7 @@ struct Packed {
     std::vector<uint32_t> l_cols;
     std::vector<uint32_t> thr;
     std::vector<int32_t> pos_col;
+    std::vector<float> wts;      // [2][w_T][slots] (empty without weights)
 };
 
 // Packs the graph for kernel variant v; returns false if v cannot take it.
@@ -198,6 +202,12 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
             const int m = fill[j]++;
             edge_slot[a] = ((pos / G) * P.cv + m) * G + (pos % G);
         }
+    if (!g.w_host.empty()) {   // learned weights into message-slot order
+        const size_t E = g.H.col.size();
+        P.wts.assign((size_t)2 * g.w_T * P.slots, 1.0f);
+        for (int h = 0; h < 2 * g.w_T; ++h)
+            for (size_t a = 0; a < E; ++a) P.wts[(size_t)h * P.slots + edge_slot[a]] = g.w_host[h * E + a];
+    }
     P.chk_idx.assign((size_t)P.pc * P.dc * G, kNoEdge);
     for (int i = 0; i < M; ++i) {
         const int p = i / G, u = i % G;
@@ -311,6 +321,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
             lamc[j] = (float)std::log((1.0 - g->priors[j]) / g->priors[j]);
     }
     const size_t o_cptr = put(blob, cptr), o_cedge = put(blob, cedge), o_lamc = put(blob, lamc);
+    const size_t o_wts = put(blob, P.wts);
     const size_t o_err = put(blob, std::vector<int32_t>(4, 0));
     void *arena = nullptr;
     e = cudaMalloc(&arena, blob.size());
@@ -349,6 +360,9 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     d.c_ptr = (const int32_t *)(base + o_cptr);
     d.c_edge = (const int32_t *)(base + o_cedge);
     d.lam_col = (const float *)(base + o_lamc);
+    d.wts = P.wts.empty() ? nullptr : (const float *)(base + o_wts);
+    d.w_T = P.wts.empty() ? 0 : g->w_T;
+    d.w_clip = g->w_clip;
     d.err_flag = (int32_t *)(base + o_err);
     g->variant = vid;
     g->groups_per_block = gpb;
@@ -629,6 +643,37 @@ int bpdc_graph_set_layout(bpdc_graph_t g, int32_t mode)
     g->layout = mode;
     const int rc = replan(g, 0, g->variant);
     if (rc != BPDC_OK) g->layout = keep;
+    return rc;
+}
+
+int bpdc_graph_set_weights(bpdc_graph_t g, const float *weights, int32_t T, float clip)
+{
+    if (!g) return fail(BPDC_ERR_INVALID_ARG, "graph is NULL");
+    if (weights && (T < 1 || T > 1000)) return fail(BPDC_ERR_INVALID_ARG, "T must be in [1, 1000]");
+    if (weights && (!(clip > 0.0f) || clip > 30.0f)) return fail(BPDC_ERR_INVALID_ARG, "clip must be in (0, 30]");
+    if (weights && g->opts.variant != 1)
+        return fail(BPDC_ERR_UNSUPPORTED, "learned weights need the product-sum check rule (variant 1)");
+    const size_t E = g->H.col.size();
+    std::vector<float> keep = g->w_host;
+    const int keep_T = g->w_T;
+    const float keep_clip = g->w_clip;
+    if (weights) {
+        g->w_host.assign(weights, weights + (size_t)2 * T * E);
+        for (float w : g->w_host)
+            if (!std::isfinite(w)) { g->w_host = keep; return fail(BPDC_ERR_INVALID_ARG, "non-finite weight"); }
+        g->w_T = T;
+        g->w_clip = clip;
+    } else {
+        g->w_host.clear();
+        g->w_T = 0;
+        g->w_clip = 0.0f;
+    }
+    const int rc = replan(g, 0, g->variant);
+    if (rc != BPDC_OK) {
+        g->w_host = keep;
+        g->w_T = keep_T;
+        g->w_clip = keep_clip;
+    }
     return rc;
 }
 

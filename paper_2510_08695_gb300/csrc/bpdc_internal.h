@@ -42,6 +42,13 @@ struct DevGraph {
     int32_t dc_enable, dc_prior;
     int32_t zero_ok;             // every prior < 1/2: zero syndrome decodes to zero at t = 0
     int32_t kernel_id;
+    // learned weights of weighted BP (product-sum only), in message-slot order:
+    // wts[0][t][slot] scales check -> variable messages, wts[1][t][slot]
+    // variable -> check messages of decoding iteration t + 1 (the last set for
+    // later iterations); variable -> check messages are clipped to +-w_clip
+    const float *wts;            // [2][w_T][slots] or null
+    int32_t w_T;
+    float w_clip;
     const uint16_t *chk_idx;     // [pc][dc][G] message slot of the check's k-th edge, or kNoEdge
     const uint8_t *var_deg;      // [pv][G] degree of the variable (0 past N)
     const float *lam;            // [pv][G] prior LLR ln((1-p)/p)

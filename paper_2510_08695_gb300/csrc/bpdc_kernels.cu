@@ -189,6 +189,7 @@ struct Lane {
     // than 64 KB of shared memory, else the word index in the group's region
     uint32_t aw[kAddrWords];
     uint32_t region_base;      // shared byte address of the group's region (wide form)
+    uint32_t slot_base;        // shared byte address of slot 0
     uint32_t vm[kVmWords];     // bit (p*CVM + m): the variable at pass p has an m-th edge
     uint32_t vvalid;           // bit p: a variable sits at pass p
     uint32_t cvalid;           // bit p: a check sits at pass p
@@ -225,6 +226,7 @@ struct Lane {
         lane_base = slot_base + 4u * (uint32_t)u;
         inf_addr = inf_word;
         region_base = slot_base - 4u * kMiscWords;
+        this->slot_base = slot_base;
         cvalid = 0;
 #pragma unroll
         for (int w = 0; w < kAddrWords; ++w) aw[w] = 0;
@@ -284,8 +286,19 @@ struct Decoder {
                 hd |= e << p;
                 const uint32_t v = (__float_as_uint(lam) & ~1u) | e;
                 const uint32_t base = ln.lane_base + p * kPass;
+                if (RULE == 1 && g.wts) {   // weighted BP: q = clip(wv[0] lambda) per edge
+                    const float *wv = g.wts + (size_t)g.w_T * g.slots;
 #pragma unroll
-                for (int m = 0; m < CVM; ++m) sts32(base + m * kSlot, (m < CMIN || ln.has(p, m)) ? v : 0u);
+                    for (int m = 0; m < CVM; ++m) {
+                        const bool on = m < CMIN || ln.has(p, m);
+                        const float q = on ? fminf(fmaxf(__ldg(wv + (p * CVM + m) * G + u) * lam, -g.w_clip), g.w_clip)
+                                           : 0.0f;
+                        sts32(base + m * kSlot, on ? ((__float_as_uint(q) & ~1u) | e) : 0u);
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < CVM; ++m) sts32(base + m * kSlot, (m < CMIN || ln.has(p, m)) ? v : 0u);
+                }
                 if (post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = lam;
             }
         }
@@ -407,7 +420,12 @@ struct Decoder {
                                 mag = fminf(mag, kLlrCap);
                                 pre += f[k];
                                 if (RC && !live) mag = f_inf();   // idle check: writes +inf back
-                                const uint32_t out = __float_as_uint(mag) ^ Sm ^ (qb[k] & 0x80000000u);
+                                uint32_t out = __float_as_uint(mag) ^ Sm ^ (qb[k] & 0x80000000u);
+                                if (g.wts && live && a != ln.inf_addr) {   // weighted BP: r *= wc
+                                    const float w = __ldg(g.wts + (size_t)(min(t, g.w_T) - 1) * g.slots +
+                                                          ((a - ln.slot_base) >> 2));
+                                    out = __float_as_uint(w * __uint_as_float(out));
+                                }
                                 if (RC) sts32(a, out);
                                 else sts32_if(a, out, a != ln.inf_addr);
                             }
@@ -439,9 +457,13 @@ struct Decoder {
                     const float Lp = pre[CVM];
                     const uint32_t e = Lp <= 0.0f ? 1u : 0u;
                     nhd |= e << p;
+                    const float *wv = (RULE == 1 && g.wts)
+                        ? g.wts + ((size_t)g.w_T + min(t + 1, g.w_T) - 1) * g.slots + (p * CVM) * G + u
+                        : nullptr;
 #pragma unroll
                     for (int m = 0; m < CVM; ++m) {
-                        const float q = (m == CVM - 1) ? pre[m] : pre[m] + suf[m + 1];
+                        float q = (m == CVM - 1) ? pre[m] : pre[m] + suf[m + 1];
+                        if (RULE == 1 && wv) q = fminf(fmaxf(__ldg(wv + m * G) * q, -g.w_clip), g.w_clip);
                         const uint32_t qv = (__float_as_uint(q) & ~1u) | e;
                         if (m < CMIN) sts32(base + m * kSlot, qv);
                         else sts32_if(base + m * kSlot, qv, ln.has(p, m));

@@ -72,3 +72,35 @@ def train_weights(graph, T: int = 20, steps: int = 50, batch: int = 4096, lr: fl
         opt.step()
         hist.append(float(loss.detach()))
     return W.detach(), hist
+
+
+def logical_error_rate(graph, shots: int, seed: int, shot_offset: int = 0, chunk: int = 100000) -> float:
+    """BP+DC logical error rate of the graph's current setting (with or
+    without learned weights) on seeded shots sampled by the library."""
+    fails = 0
+    done = 0
+    dev = torch.device("cuda", graph.device)
+    while done < shots:
+        n = min(chunk, shots - done)
+        syn, obs, _ = graph.sample(n, seed, shot_offset + done)
+        cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+        graph.decode(syn, shot_offset + done, obs_true=obs, counters=cnt)
+        fails += int(cnt[1])
+        done += n
+    return fails / shots
+
+
+def select_weights(graph, weights, clip: float = 20.0, shots: int = 100000, seed: int = 99,
+                   shot_offset: int = 1 << 40):
+    """Keeps learned weights only where they do no worse: BP+DC logical error
+    rates with and without them on the same held-out shots (offsets far from
+    the training shots); the graph is left with the better setting.  Returns
+    (kept, ler_weighted, ler_plain)."""
+    graph.set_weights(None)
+    ler_plain = logical_error_rate(graph, shots, seed, shot_offset)
+    graph.set_weights(weights, clip)
+    ler_w = logical_error_rate(graph, shots, seed, shot_offset)
+    kept = ler_w <= ler_plain
+    if not kept:
+        graph.set_weights(None)
+    return kept, ler_w, ler_plain

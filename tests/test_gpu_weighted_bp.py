@@ -115,3 +115,55 @@ def test_training_lowers_the_loss(setup):
     Wt, hist = wbp.train_weights(g, T=10, steps=12, batch=1024, lr=0.02, seed=SEED + 41)
     assert Wt.shape == (2, 10, P.E)
     assert np.mean(hist[-3:]) < hist[0], hist
+
+
+def test_weighted_decode_matches_reference(setup):
+    """BP (no DC) with learned weights inside the decoder: the iteration at
+    which the hard decision first reproduces the syndrome and the posterior
+    there equal the reference's, on shots whose reference posteriors stay
+    away from 0 up to that iteration."""
+    pkg, wbp, P, g, e, s, T, W = setup
+    gd = pkg.Graph.from_problem(P, pkg.Options(variant=1, max_iter=T, dc_enable=0))
+    gd.set_weights(torch.tensor(W, dtype=torch.float32), clip=20.0)
+    out = gd.decode(to_dev(s), 0, posterior=True)
+    it = out["iterations"].cpu().numpy() & 0xFFFF
+    st = out["status"].cpu().numpy()
+    post = out["posterior_llr"].cpu().numpy().astype(np.float64)
+    rp = ref.forward(P.H, P.priors, s, torch.tensor(W)).numpy()       # [B, T, N]
+    H = P.H.toarray().astype(np.int64)
+    lam = np.log((1 - P.priors) / P.priors)
+    checked = 0
+    for b in range(s.shape[0]):
+        hist = [lam] + [rp[b, t] for t in range(T)]                   # posterior after 0..T iterations
+        conv = [t for t in range(T + 1) if (((H @ (hist[t] <= 0)) % 2) == s[b]).all()]
+        t_ref = conv[0] if conv else None
+        upto = (t_ref if t_ref is not None else T)
+        if min(np.abs(h).min() for h in hist[1:upto + 1] or [lam]) < 1e-3:
+            continue
+        checked += 1
+        if t_ref is None:
+            assert st[b] == 2 and it[b] == T
+            ref_post = hist[T]
+        else:
+            assert st[b] == 0 and it[b] == t_ref, (b, st[b], it[b], t_ref)
+            ref_post = hist[t_ref]
+        assert (np.abs(post[b] - ref_post) / np.maximum(np.abs(ref_post), 1.0)).max() < 1e-4
+    assert checked > 40
+
+
+def test_weights_need_the_product_sum_rule(setup):
+    pkg, wbp, P, g, e, s, T, W = setup
+    gm = pkg.Graph.from_problem(P, pkg.Options(variant=0))
+    with pytest.raises(pkg.BpdcError):
+        gm.set_weights(torch.ones(2, T, P.E), clip=20.0)
+
+
+def test_learned_weights_are_kept_only_when_no_worse(setup):
+    pkg, wbp, P, g, e, s, T, W = setup
+    gd = pkg.Graph.from_problem(P, pkg.Options(variant=1, max_iter=50))
+    Wt, _ = wbp.train_weights(gd, T=10, steps=8, batch=1024, lr=0.02, seed=SEED + 42)
+    kept, ler_w, ler_p = wbp.select_weights(gd, Wt, shots=20000)
+    assert kept == (ler_w <= ler_p)
+    # the graph is left with the better setting
+    ler_now = wbp.logical_error_rate(gd, 20000, 99, 1 << 40)
+    assert ler_now == min(ler_w, ler_p) if kept else ler_now == ler_p
