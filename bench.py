@@ -40,6 +40,7 @@ CODES = ["bb144", "bb72", "hgp2500"]
 ALPHA, T_ITER = 0.625, 50
 SMEM_BYTES_PER_CLK_PER_SM = 128   # 32 banks x 4 B
 SERVE_ROUNDS, SERVE_P, SERVE_T_ITER, SERVE_REQUESTS = 12, 1e-3, 1000, 600
+WBP_T, WBP_BATCH, WBP_STEPS, WBP_LR, WBP_EVAL_SHOTS = 20, 4096, 60, 0.01, 200000
 EDGE_UPDATE_BYTES = 16            # 2 x 4 B read + 2 x 4 B written per edge and iteration
 
 
@@ -74,7 +75,9 @@ def extrapolate_cpu(samples, shots_per_point: int) -> float:
 
 
 def oracle_sample_plan(code: str) -> int:
-    return 400 if code == "hgp2500" else 4000
+    """Shots of each (code, p) point the CPU baseline decodes (about 10 s of
+    work on 16 cores); the reference arm decodes a quarter of it per step."""
+    return 1600 if code == "hgp2500" else 16000
 
 
 def profiled_traffic(kernel_id: int, shots: int, edge_updates: int):
@@ -452,6 +455,33 @@ def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
                        "server_slots": 4, "identical_results": same,
                        "circuit_level_status_counts": torch.bincount(st.long(), minlength=3).tolist()}
     line["p99_us_per_shot"] = lat["server"]["p99_us"]
+
+    # ---- differentiable weighted BP: training throughput (forward + adjoint
+    # kernels, batches of 4096 sampled shots, T = 20) and BP+DC with the learned
+    # weights against plain BP+DC on held-out shots
+    import bpdc_inputs as bi
+    from paper_2510_08695_gb300 import wbp
+    P6 = bi.bb_problem("bb144", 0.06)
+    gw = pkg.Graph.from_problem(P6, pkg.Options(variant=1, max_iter=T_ITER))
+    wbp.train_weights(gw, T=WBP_T, steps=2, batch=WBP_BATCH, lr=WBP_LR, seed=SEED + 60)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    W, hist = wbp.train_weights(gw, T=WBP_T, steps=WBP_STEPS, batch=WBP_BATCH, lr=WBP_LR, seed=SEED + 61)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    ler = {}
+    for pp in (0.04, 0.06, 0.08):
+        ge = pkg.Graph.from_problem(bi.bb_problem("bb144", pp), pkg.Options(variant=1, max_iter=T_ITER))
+        kept, lw, lp = wbp.select_weights(ge, W, shots=WBP_EVAL_SHOTS, seed=SEED + 62)
+        ler[f"bb144@{pp:g}"] = {"learned": lw, "plain": lp, "learned_weights_used": kept}
+    line["weighted_bp"] = {
+        "config": f"BB[[144,12,12]] code capacity, product-sum, {WBP_T} unrolled iterations, weights 2 x {WBP_T} x "
+                  f"{P6.E} (per edge, iteration and direction), Adam lr {WBP_LR}, batches of {WBP_BATCH} shots "
+                  f"sampled at p=0.06, BCE on the posteriors of every iteration, checkpoints every 5 iterations",
+        "train_steps": WBP_STEPS, "train_s": t_train, "train_shots_per_s": WBP_STEPS * WBP_BATCH / t_train,
+        "loss_first": hist[0], "loss_last": hist[-1],
+        "ler_bp_dc_held_out": ler, "held_out_shots": WBP_EVAL_SHOTS,
+        "rule": "learned weights are used only where their BP+DC logical error rate is no worse than plain"}
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample of the workload
     import oracle
