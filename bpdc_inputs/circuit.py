@@ -34,7 +34,7 @@ import scipy.sparse as sp
 from . import codes
 
 __all__ = ["bb_perms", "syndrome_circuit", "simulate_dem", "dcm_block_form", "ddm_block_form",
-           "circuit_level_problem"]
+           "stabilizer_rows", "window_trivial_errors", "ddm_local_window", "circuit_level_problem"]
 
 
 def bb_perms(name: str):
@@ -273,13 +273,58 @@ def _dem_in_block_order(name: str, T: int, p: float):
     return H, obs[order].astype(np.uint8), pm[order]
 
 
-def circuit_level_problem(name: str, T: int, p: float, extra_block: bool | None = None) -> codes.Problem:
-    """(H_DCM, H_DDM (w = 3), O, priors) of the circuit-level model: the
-    simulated mechanisms in the column order of Eq. C1 (verified equal as
-    sets), D from Eq. D2."""
+def stabilizer_rows(name: str, T: int) -> np.ndarray:
+    """The X-stabilizer rows of H_DDM: H_X = (A | B) on the data columns before
+    every round and on the final data columns."""
+    n, b = _blocks(name)
+    h = n // 2
+    N = T * 5 * n + n
+    hx = (np.hstack([b["A"], b["B"]]) % 2).astype(np.uint8)
+    D = np.zeros(((T + 1) * h, N), dtype=np.uint8)
+    for r in range(T + 1):
+        D[r * h:(r + 1) * h, r * 5 * n:r * 5 * n + n] = hx
+    return D
+
+
+@functools.lru_cache(maxsize=None)
+def window_trivial_errors(name: str, w: int, t_loc: int = 3) -> tuple:
+    """Trivial errors of weight <= w of the t_loc-round model (App. D's local
+    temporal window), as sorted column tuples of that model."""
+    from . import native
+    H = dcm_block_form(name, t_loc)
+    _, O, _ = _dem_in_block_order(name, t_loc, 1e-3)
+    return tuple(sorted(native.trivial_errors(H, O.T, w)))
+
+
+def ddm_local_window(name: str, T: int, w: int, t_loc: int = 3) -> sp.csr_matrix:
+    """H_DDM from the stabilizers and every trivial error of weight <= w found
+    in a t_loc-round window, translated to each of the T - t_loc + 1 start
+    rounds (App. D).  Columns of the window's model map to the full model by a
+    shift of 5n per round (the window's final data block becomes the next
+    round's data-before-round block, or the final block)."""
+    n = bb_perms(name)[0]
+    if T < t_loc:
+        raise ValueError("T must be at least t_loc")
+    pats = window_trivial_errors(name, w, t_loc)
+    rows = {tuple(np.nonzero(r)[0]) for r in stabilizer_rows(name, T)}
+    for r in range(T - t_loc + 1):
+        for pat in pats:
+            rows.add(tuple(c + 5 * n * r for c in pat))
+    rows = sorted(rows)
+    N = T * 5 * n + n
+    ptr = np.cumsum([0] + [len(r) for r in rows])
+    col = np.fromiter((c for r in rows for c in r), dtype=np.int64, count=int(ptr[-1]))
+    return sp.csr_matrix((np.ones(len(col), dtype=np.uint8), col, ptr), shape=(len(rows), N))
+
+
+def circuit_level_problem(name: str, T: int, p: float, extra_block: bool | None = None,
+                          w: int = 3) -> codes.Problem:
+    """(H_DCM, H_DDM, O, priors) of the circuit-level model: the simulated
+    mechanisms in the column order of Eq. C1 (verified equal as sets); D from
+    Eq. D2 for w = 3, else from the local-window search for weight <= w."""
     H, O, pm = _dem_in_block_order(name, T, float(p))
     if extra_block is None:
         extra_block = name == "bb108"
-    D = ddm_block_form(name, T, extra_block)
-    return codes.Problem(f"{name}_circuit_T{T}_p{p:g}", codes._csr(H), codes._csr(D), codes._csr(O.T),
-                         pm.astype(np.float64), dict(T=T, p=p, model="circuit"))
+    D = ddm_block_form(name, T, extra_block) if w == 3 else ddm_local_window(name, T, w)
+    return codes.Problem(f"{name}_circuit_T{T}_p{p:g}_w{w}", codes._csr(H), codes._csr(D), codes._csr(O.T),
+                         pm.astype(np.float64), dict(T=T, p=p, w=w, model="circuit"))

@@ -103,3 +103,73 @@ def test_every_weight3_trivial_error_is_a_row(name, extra, complete):
     assert len(triv) > 0
     assert (triv <= rows) == complete, (len(triv), len(triv - rows))
     assert rows <= triv     # and every weight-3 row is a trivial error
+
+
+# ---------------------------------------------------------------------------
+# H_DDM for w = 4, 5 by the local-window search (App. D)
+
+@pytest.mark.parametrize("name", ["bb72", "bb144", "bb108"])
+def test_window_search_reproduces_the_printed_ddm(name):
+    """Weight <= 3 trivial errors of a 3-round window, translated to every
+    start round, plus the stabilizers, are exactly the rows of Eq. D2 (with
+    the extra row block for [[108,8,10]])."""
+    T = 5
+    Dw = circuit.ddm_local_window(name, T, 3).toarray()
+    Dp = circuit.ddm_block_form(name, T, name == "bb108")
+    assert {tuple(np.nonzero(r)[0]) for r in Dw} == {tuple(np.nonzero(r)[0]) for r in Dp}
+
+
+@pytest.mark.parametrize("w", [4, 5])
+def test_window_translation_equals_direct_search(w):
+    """App. D: every trivial error of weight <= 5 lies within 3 consecutive
+    rounds, so the translated window patterns equal a direct search of the
+    whole 5-round model."""
+    from bpdc_inputs import native
+    P = circuit.circuit_level_problem("bb72", 5, 1e-3)
+    direct = native.trivial_errors(P.H, P.L, w)
+    rows = {tuple(np.nonzero(r)[0]) for r in circuit.ddm_local_window("bb72", 5, w).toarray()}
+    stab = {tuple(np.nonzero(r)[0]) for r in circuit.stabilizer_rows("bb72", 5)}
+    assert direct == rows - stab
+
+
+def _mitm_up_to_4(H, O):
+    """Independent check: weight-3 and weight-4 trivial errors by meet in the
+    middle over column pairs (column signature = its H and O column)."""
+    S = np.concatenate([H, O], axis=0).T.astype(np.uint8)
+    N = S.shape[0]
+    key = [r.tobytes() for r in np.packbits(S, axis=1)]
+    single = {}
+    for j in range(N):
+        single.setdefault(key[j], []).append(j)
+    pairs = {}
+    out = set()
+    for a in range(N):
+        x = np.packbits(S[a + 1:] ^ S[a], axis=1)
+        for off in range(x.shape[0]):
+            b = a + 1 + off
+            kk = x[off].tobytes()
+            pairs.setdefault(kk, []).append((a, b))
+            for c in single.get(kk, ()):
+                if c != a and c != b:
+                    out.add(tuple(sorted((a, b, c))))
+    for lst in pairs.values():
+        for i in range(len(lst)):
+            for k in range(i + 1, len(lst)):
+                u = set(lst[i]) | set(lst[k])
+                if len(u) == 4:
+                    out.add(tuple(sorted(u)))
+    return out
+
+
+def test_native_search_matches_meet_in_the_middle():
+    from bpdc_inputs import native
+    P = circuit.circuit_level_problem("bb72", 2, 1e-3)
+    H, O = P.H.toarray(), P.L.toarray()
+    assert native.trivial_errors(P.H, P.L, 4) == _mitm_up_to_4(H, O)
+
+
+def test_local_window_ddm_identities():
+    P = circuit.circuit_level_problem("bb72", 4, 1e-3, w=5)
+    H, D, O = (m.toarray().astype(np.int64) for m in (P.H, P.D, P.L))
+    assert not ((D @ H.T) % 2).any() and not ((D @ O.T) % 2).any()
+    assert set(np.unique(D.sum(1))) == {3, 4, 5, 6}

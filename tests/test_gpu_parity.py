@@ -388,3 +388,14 @@ def test_circuit_level_parity_bb144_full_size(pkg, oracle_mod):
     ref["well_conditioned"] = np.concatenate(wc)
     rep = _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.5)
     assert rep["status_ref"][1] > 10
+
+
+def test_circuit_level_parity_bb72_w5(pkg, oracle_mod):
+    """H_DDM from the local-window search for trivial errors of weight <= 5
+    (App. D; the paper's circuit-level setting): 60 696 rows on BB72, 6 rounds."""
+    from bpdc_inputs import circuit
+    P = circuit.circuit_level_problem("bb72", 6, 3e-3, w=5)
+    g, s, o, out, ref = _run(pkg, oracle_mod, P, 300, dict(ms_scale=0.625, max_iter=1000))
+    assert g.info["kernel_id"] == 13 and P.D.shape[0] > 50000
+    rep = _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.5)
+    assert rep["status_ref"][1] > 20
