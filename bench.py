@@ -456,6 +456,35 @@ def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
                        "circuit_level_status_counts": torch.bincount(st.long(), minlength=3).tolist()}
     line["p99_us_per_shot"] = lat["server"]["p99_us"]
 
+    # ---- CUDA graph: a small request decoded by a direct multi-batch call
+    # against the same allocation-free call replayed from a captured graph
+    bb72b = [b for b in batches if b["code"] == "bb72" and b["p"] == 0.05][0]
+    gg = bb72b["graph"]
+    nb = 64
+    sb = bb72b["syndromes"][:nb].clone()
+    ob = gg.alloc_outputs(nb)
+    it = [dict(graph=gg, syndromes=sb, shot_offset=0, out=ob)]
+    pkg.decode_multi_noalloc(it)
+    torch.cuda.synchronize()
+    cs = torch.cuda.Stream()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=cs):
+        pkg.decode_multi_noalloc(it)
+    lat_g = {}
+    for name, fn in (("direct_call", lambda: pkg.decode_multi_noalloc(it)), ("graph_replay", cg.replay)):
+        for _ in range(20):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(300):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        lat_g[name] = {"p50_us": float(np.percentile(ts, 50) * 1e6), "p99_us": float(np.percentile(ts, 99) * 1e6)}
+    line["cuda_graph"] = {"request": f"{nb} BB[[72,12,6]] shots at p=0.05, call to results on the device",
+                          **lat_g}
+
     # ---- differentiable weighted BP: training throughput (forward + adjoint
     # kernels, batches of 4096 sampled shots, T = 20) and BP+DC with the learned
     # weights against plain BP+DC on held-out shots

@@ -218,6 +218,12 @@ int bpdc_decode_multi(const bpdc_batch *batches, int32_t n_batches, void *stream
  *   - Every call reuses the same array (the work counter is cleared at the
  *     start of each call).  Calls whose launches overlap on the GPU, e.g. on
  *     two streams, race on it: keep such calls ordered on one stream.
+ *   - The call issues two kernel launches and nothing else: a setup kernel that
+ *     receives the batch descriptors as kernel parameters, writes them into the
+ *     array and clears the counter, then the decode kernel.  It can therefore
+ *     be captured into a CUDA graph (after a first uncaptured call on the
+ *     device); each replay decodes whatever the captured syndrome buffers hold
+ *     into the captured output buffers.
  * Results equal those of bpdc_decode_multi on the same batches. */
 int bpdc_decode_multi_noalloc(const bpdc_batch *batches, int32_t n_batches, void *stream);
 

@@ -893,6 +893,21 @@ static cudaError_t static_scratch_address(void **out)
     return cudaSuccess;
 }
 
+// Descriptors of an allocation-free launch, passed by value: the launch
+// copies them into its parameter buffer, so a captured CUDA graph replays
+// them without reading host memory again.
+struct StaticSetup {
+    BatchDesc d[kStaticBatches];
+    int n;
+};
+
+__global__ void static_setup_kernel(StaticSetup st, BatchDesc *dst, unsigned long long *work)
+{
+    const int i = threadIdx.x;
+    if (i < st.n) dst[i] = st.d[i];
+    if (i == 0) *work = 0ull;   // the work counter starts at zero
+}
+
 cudaError_t launch_variant_static(int id, const BatchDesc *host_descs, int n, int64_t total, int grid,
                                   int smem_bytes, cudaStream_t s)
 {
@@ -902,10 +917,11 @@ cudaError_t launch_variant_static(int id, const BatchDesc *host_descs, int n, in
     if (e != cudaSuccess) return e;
     auto *work = reinterpret_cast<unsigned long long *>(base);
     auto *descs = reinterpret_cast<BatchDesc *>(static_cast<unsigned char *>(base) + 256);
-    e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), s);   // the counter must start at zero
-    if (e != cudaSuccess) return e;
-    // host_descs is pageable: the copy has consumed it when the call returns
-    e = cudaMemcpyAsync(descs, host_descs, sizeof(BatchDesc) * n, cudaMemcpyHostToDevice, s);
+    StaticSetup st;
+    for (int i = 0; i < n; ++i) st.d[i] = host_descs[i];
+    st.n = n;
+    static_setup_kernel<<<1, 32, 0, s>>>(st, descs, work);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     LaunchDesc ld{};
     ld.batches = descs;
