@@ -90,15 +90,18 @@ def profiled_traffic(kernel_id: int, shots: int, edge_updates: int):
     import glob
     import hashlib
     src = os.path.join(ROOT, "paper_2510_08695_gb300", "csrc", "bpdc_kernels.cu")
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(src, "rb").read()
+    # the device code and the variant table (everything before the host-side
+    # kVariants array); host launch code below it does not change the kernels
+    cur = hashlib.sha256(text[:text.index(b"static const Variant kVariants[]")]).hexdigest()[:16]
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "decode_kernel_*.md"))):
         text = open(path).read()
         if f"# decode_kernel variant {kernel_id} " not in text:
             continue
         kv = dict(line.split(": ", 1) for line in text.splitlines()
                   if ": " in line and line.split(": ", 1)[0] in
-                  ("traffic_bytes_per_shot", "smem_wavefront_bytes_per_edge_update", "kernel_source_sha256_16"))
-        if kv.get("kernel_source_sha256_16") != cur or "traffic_bytes_per_shot" not in kv:
+                  ("traffic_bytes_per_shot", "smem_wavefront_bytes_per_edge_update", "kernel_device_source_sha256_16"))
+        if kv.get("kernel_device_source_sha256_16") != cur or "traffic_bytes_per_shot" not in kv:
             return None, None, os.path.basename(path)
         smem = float(kv["smem_wavefront_bytes_per_edge_update"]) * edge_updates \
             if "smem_wavefront_bytes_per_edge_update" in kv else None
@@ -525,10 +528,25 @@ def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
         oracle.decode_batch(b["P"], s, b["shot_offset"], opts)
         samples.append((n, time.perf_counter() - t))
     cpu = extrapolate_cpu(samples, args.shots_per_point)
-    line["cpu_baseline"] = {"value": cpu, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+    cores = oracle.max_threads()
+    # one core, on a sixteenth of the sample
+    oracle.set_threads(1)
+    samples1 = []
+    for b in batches:
+        n = max(1, oracle_sample_plan(b["code"]) // 16)
+        _, s, _ = sample_shots(b["P"], SEED, b["shot_offset"], n)
+        t = time.perf_counter()
+        oracle.decode_batch(b["P"], s, b["shot_offset"], opts)
+        samples1.append((n, time.perf_counter() - t))
+    oracle.set_threads(cores)
+    line["cpu_baseline"] = {"value": cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"first {oracle_sample_plan('bb72')} (BB) / {oracle_sample_plan('hgp2500')} "
                                       "(HGP) shots of each (code, p) point, CPU sampler, extrapolated per point "
-                                      f"to {args.shots_per_point} shots; {sum(t for _, t in samples):.1f} s of CPU"}
+                                      f"to {args.shots_per_point} shots; {sum(t for _, t in samples):.1f} s of CPU",
+                            "value_1_core": extrapolate_cpu(samples1, args.shots_per_point),
+                            "sample_1_core": f"first {oracle_sample_plan('bb72') // 16} (BB) / "
+                                             f"{oracle_sample_plan('hgp2500') // 16} (HGP) shots of each point, "
+                                             f"{sum(t for _, t in samples1):.1f} s"}
 
 
 if __name__ == "__main__":

@@ -193,6 +193,9 @@ class Oracle:
     def max_threads(self) -> int:
         return int(self.lib.oracle_max_threads())
 
+    def set_threads(self, n: int) -> None:
+        self.lib.oracle_set_threads(ctypes.c_int(int(n)))
+
 
 def _load() -> Oracle:
     global _lib
@@ -219,3 +222,8 @@ def decode_batch(*args, **kw):
 
 def max_threads() -> int:
     return _load().max_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's loop over shots (timing of the CPU baseline)."""
+    _load().set_threads(n)

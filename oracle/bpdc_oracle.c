@@ -389,6 +389,16 @@ int oracle_decode_batch(const oracle_problem *P, const oracle_opts *o, int64_t B
     return 0;
 }
 
+/* Thread count of the OpenMP loop over shots (n >= 1); timing only. */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP
