@@ -362,12 +362,52 @@ def main():
             "gpu_launches": args.steps * len(groups),
             "clocks": clk}
 
-    if rank == 0 and not args.no_extras:
+    if not args.no_extras:
+        line["e2e"] = e2e_leg(args, pkg, torch, batches, groups, stream, world)
+    # the remaining legs characterise one GPU (and the host CPU): N = 1 only
+    if rank == 0 and world == 1 and not args.no_extras:
         extras(args, pkg, torch, batches, groups, stream, line, value, fails)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def e2e_leg(args, pkg, torch, batches, groups, stream, world):
+    """The metric end to end through the public API: every step copies this
+    rank's syndromes from pinned host memory, decodes them and copies the
+    corrections, status and logical flips back; barrier and max over ranks."""
+    host = []
+    for b in batches:
+        hs = b["syndromes"].cpu().pin_memory()
+        ho = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in b["out"].items()
+              if k in ("corrections", "status", "logical_flips")}
+        host.append((b, hs, ho))
+    h2d = sum(hs.numel() * hs.element_size() for _, hs, _ in host)
+    d2h = sum(t.numel() * t.element_size() for _, _, ho in host for t in ho.values())
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        for b, hs, _ in host:
+            b["syndromes"].copy_(hs, non_blocking=True)
+        for vid, items in sorted(groups.items()):
+            pkg.decode_multi(items, stream)
+        for b, _, ho in host:
+            for k, t in ho.items():
+                t.copy_(b["out"][k], non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    e2e = len(batches) * args.shots_per_point * args.steps * world / (ms / 1e3)
+    return {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d * world, "d2h_bytes_per_step": d2h * world}
 
 
 def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
@@ -394,30 +434,6 @@ def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
                             "identical_outputs": same}
     line["ler"] = {f"{b['code']}@{b['p']}": fails[id(b)] / args.shots_per_point for b in batches}
     line["failures_per_step"] = tot_fail
-
-    # ---- end to end through the public API with pinned host buffers
-    host = []
-    for b in batches:
-        hs = b["syndromes"].cpu().pin_memory()
-        ho = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in b["out"].items()
-              if k in ("corrections", "status", "logical_flips")}
-        host.append((b, hs, ho))
-    h2d = sum(hs.numel() * hs.element_size() for _, hs, _ in host)
-    d2h = sum(t.numel() * t.element_size() for _, _, ho in host for t in ho.values())
-    torch.cuda.synchronize()
-    t0.record(stream)
-    for _ in range(args.steps):
-        for b, hs, _ in host:
-            b["syndromes"].copy_(hs, non_blocking=True)
-        for vid, items in sorted(groups.items()):
-            pkg.decode_multi(items, stream)
-        for b, _, ho in host:
-            for k, t in ho.items():
-                t.copy_(b["out"][k], non_blocking=True)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    e2e = len(batches) * args.shots_per_point * args.steps / (t0.elapsed_time(t1) / 1e3)
-    line["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- serving: seeded Poisson trace mixing circuit-level BB[[144,12,12]]
     # requests (12 rounds, p = 1e-3, T_iter = 1000) with code-capacity
