@@ -1,5 +1,5 @@
-"""Pins of the plain-PyTorch weighted-BP reference (oracle/weighted_bp.py)
-before it judges the CUDA adjoint: unit weights reproduce the FP64 oracle's
+"""Pins of the plain-PyTorch weighted-BP reference (oracle/weighted_bp.py),
+which the CUDA forward and adjoint are checked against: unit weights reproduce the FP64 oracle's
 product-sum BP iteration by iteration, zero check weights leave the priors,
 a two-edge check has a closed form, and autograd agrees with central finite
 differences."""
