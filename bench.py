@@ -92,8 +92,13 @@ def profiled_traffic(kernel_id: int, shots: int, edge_updates: int):
     src = os.path.join(ROOT, "paper_2510_08695_gb300", "csrc", "bpdc_kernels.cu")
     text = open(src, "rb").read()
     # the device code and the variant table (everything before the host-side
-    # kVariants array); host launch code below it does not change the kernels
-    cur = hashlib.sha256(text[:text.index(b"static const Variant kVariants[]")]).hexdigest()[:16]
+    # kVariants array; host launch code below it does not change the kernels),
+    # without comments and blank lines
+    import re
+    code = text[:text.index(b"static const Variant kVariants[]")].decode()
+    code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", code, flags=re.S))
+    code = "\n".join(line.rstrip() for line in code.splitlines() if line.strip())
+    cur = hashlib.sha256(code.encode()).hexdigest()[:16]
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "decode_kernel_*.md"))):
         text = open(path).read()
         if f"# decode_kernel variant {kernel_id} " not in text:

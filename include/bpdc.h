@@ -227,7 +227,7 @@ int bpdc_decode_multi(const bpdc_batch *batches, int32_t n_batches, void *stream
  * Results equal those of bpdc_decode_multi on the same batches. */
 int bpdc_decode_multi_noalloc(const bpdc_batch *batches, int32_t n_batches, void *stream);
 
-/* Cut selection alone (lines 4-7 of Algorithm 1) from given posterior LLRs:
+/* Cut selection alone (the selection step of Algorithm 1) from given posterior LLRs:
  * posterior_llr device [B][N] floats, cut_out device [B][ceil(N/32)] bits.
  * Uses the graph's D, tie_rel and tie_seed. */
 int bpdc_cut_select(bpdc_graph_t g, int64_t B, const float *posterior_llr, uint64_t shot_offset,

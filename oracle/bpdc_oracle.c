@@ -243,7 +243,7 @@ int oracle_bp(const oracle_problem *P, const oracle_opts *o, const uint8_t *s, c
     return ok;
 }
 
-/* Lines 4-7 of Algorithm 1: for every row h of D pick argmin_{i in supp h}
+/* The selection step of Algorithm 1: for every row h of D pick argmin_{i in supp h}
  * p_hat_i (= argmax of the posterior LLR) and add it to the cut set.  The
  * union makes the result independent of the row order. */
 void oracle_dc_select(const oracle_problem *P, const oracle_opts *o, const double *post,
@@ -277,16 +277,16 @@ static int decode_shot(const oracle_problem *P, const oracle_opts *o, const tann
 {
     const int N = P->N, M = P->M;
     int iters = 0;
-    /* line 1 */
+    /* first BP run */
     int ok = bp_run(g, s, lam, o->max_iter, o->variant, o->alpha, 1, e_hat, post, &iters, q, r);
     *it1 = iters; *it2 = 0;
     if (post1) memcpy(post1, post, sizeof(double) * (size_t)N);
     memset(cut, 0, (size_t)N);
-    if (ok) return 0;            /* lines 2-3 */
+    if (ok) return 0;            /* converged: no cut */
     if (!o->dc_enable) return 2;
-    /* lines 4-7 */
+    /* cut selection */
     oracle_dc_select(P, o, post, shot, cut);
-    /* priors of the second run (line 9): p, or the first-run posterior */
+    /* priors of the second run (Sec. III.B): p, or the first-run posterior */
     for (int j = 0; j < N; ++j) {
         if (o->dc_prior == 0) {
             lam2[j] = lam[j];
@@ -298,7 +298,7 @@ static int decode_shot(const oracle_problem *P, const oracle_opts *o, const tann
         }
     }
     if (o->cut_form == 0) {
-        /* lines 8-10: DeleteColumns, DeleteEntries, BP, PadWithZeros */
+        /* second run on the cut graph: DeleteColumns, DeleteEntries, BP, PadWithZeros */
         int nk = 0;
         for (int j = 0; j < N; ++j) keep[j] = cut[j] ? -1 : nk++;
         int ne = 0;

@@ -33,7 +33,7 @@
 // sign and no parity, which is the column deletion of Algorithm 1 and the
 // zero prior of Algorithm 2.  Denormals must not be flushed (no -ftz).
 //
-// Degeneracy cutting (Algorithm 1 lines 4-7): on failure every row of D
+// Degeneracy cutting (the selection step of Algorithm 1): on failure every row of D
 // gathers the tagged L^T of its support from slot 0, takes the windowed
 // maximum, breaks ties with the SplitMix64 hash of (shot, row) and sets the
 // winner's bit in a shared cut mask; BP runs again with cut variables pinned
@@ -98,7 +98,7 @@ struct Group {
     }
 };
 
-// The cut of Algorithm 1 lines 4-7 for one shot: every row of D picks the
+// The cut of Algorithm 1 for one shot: every row of D picks the
 // support variable of largest posterior LLR (windowed, hashed tie-break;
 // candidates in ascending column order) and marks it.  load(a, e) returns the
 // posterior of D entry a (e = its packed slot | position word); mark(a, e)
