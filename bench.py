@@ -52,8 +52,20 @@ def shard_offset(rank: int, shots_per_point: int) -> int:
     return rank * shots_per_point
 
 
+# restricted profiling case outside the default workload: the circuit-level
+# model of the serving leg on its own (kernel variant 13)
+CIRCUIT_CASE = "circuit_bb144"
+
+
+def case_t_iter(only) -> int:
+    return SERVE_T_ITER if only == CIRCUIT_CASE else T_ITER
+
+
 def workload_problems(only=None, p_only=None):
     import bpdc_inputs as bi
+    if only == CIRCUIT_CASE:
+        from bpdc_inputs import circuit
+        return [(CIRCUIT_CASE, SERVE_P, circuit.circuit_level_problem("bb144", SERVE_ROUNDS, SERVE_P))]
     probs = []
     for code in CODES:
         if only and code != only:
@@ -206,10 +218,16 @@ def config_dict(args, world):
     n_points = len(workload_problems(getattr(args, "only", None), getattr(args, "p", None)))
     restricted = "" if n_points == len(CODES) * len(P_VALUES) else \
         f" [restricted to code={getattr(args, 'only', None)} p={getattr(args, 'p', None)}]"
-    return {"workload": "batched code capacity across uneven codes: BB[[144,12,12]], BB[[72,12,6]], "
-                        "HGP of a seeded (3,4)-regular n=40 code (n=2500, k=148); p=0.01..0.10 (10 values); "
-                        f"{args.shots_per_point} shots per (code,p) per GPU; normalized min-sum alpha=0.625, "
-                        "T_iter=50, DC on failure, second BP on priors p" + restricted,
+    if getattr(args, "only", None) == CIRCUIT_CASE:
+        text = (f"circuit-level BB[[144,12,12]], {SERVE_ROUNDS} rounds, p={SERVE_P:g} (detector model derived from "
+                f"the depth-8 syndrome circuit, H_DDM w=3); {args.shots_per_point} shots per GPU; normalized "
+                f"min-sum alpha=0.625, T_iter={SERVE_T_ITER}, DC on failure [restricted profiling case]")
+    else:
+        text = ("batched code capacity across uneven codes: BB[[144,12,12]], BB[[72,12,6]], "
+                "HGP of a seeded (3,4)-regular n=40 code (n=2500, k=148); p=0.01..0.10 (10 values); "
+                f"{args.shots_per_point} shots per (code,p) per GPU; normalized min-sum alpha=0.625, "
+                "T_iter=50, DC on failure, second BP on priors p" + restricted)
+    return {"workload": text,
             "shots_per_step": n_points * args.shots_per_point * world,
             "launch": "persistent multi-batch launches (one per kernel variant), device work counter",
             "l2": "inputs larger than L2 (no flush)",
@@ -224,7 +242,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shots-per-point", type=int, default=1_000_000)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/latency/cpu legs")
-    ap.add_argument("--only", choices=CODES, default=None,
+    ap.add_argument("--only", choices=CODES + [CIRCUIT_CASE], default=None,
                     help="restrict the workload to one code (small profiling cases; not a bench line)")
     ap.add_argument("--p", type=float, default=None, help="restrict the workload to one error rate")
     args = ap.parse_args()
@@ -254,7 +272,7 @@ def main():
     spp = args.shots_per_point
     off = shard_offset(rank, spp)
     probs = workload_problems(args.only, args.p)
-    opts = pkg.Options(ms_scale=ALPHA, max_iter=T_ITER)
+    opts = pkg.Options(ms_scale=ALPHA, max_iter=case_t_iter(args.only))
     batches = []
     for code, p, P in probs:
         g = pkg.Graph.from_problem(P, opts, device=local)
