@@ -131,6 +131,7 @@ namespace {
 struct Packed {
     int G, pc, pv, dc, cv, slots, cmw, region, KW, NW, MW;
     std::vector<uint16_t> chk_idx;
+    std::vector<uint16_t> chk_word;
     std::vector<uint8_t> var_deg;
     std::vector<float> lam;
     std::vector<int32_t> d_ptr;
@@ -214,6 +215,9 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
         for (int a = g.H.ptr[i]; a < g.H.ptr[i + 1]; ++a)
             P.chk_idx[((size_t)p * P.dc + lay.edge_round[a]) * G + u] = (uint16_t)edge_slot[a];
     }
+    P.chk_word.resize(P.chk_idx.size());
+    for (size_t k = 0; k < P.chk_idx.size(); ++k)
+        P.chk_word[k] = P.chk_idx[k] == kNoEdge ? (uint16_t)2 : (uint16_t)(12 + P.chk_idx[k]);   // 12 misc words
     P.var_deg.assign((size_t)npos, 0xFF);   // 0xFF: no variable at this position
     P.lam.assign((size_t)npos, std::numeric_limits<float>::infinity());
     P.pos_col.assign((size_t)npos, -1);
@@ -305,6 +309,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     // device arena
     std::vector<char> blob;
     const size_t o_chk = put(blob, P.chk_idx), o_deg = put(blob, P.var_deg), o_lam = put(blob, P.lam);
+    const size_t o_chkw = put(blob, P.chk_word);
     const size_t o_dptr = put(blob, P.d_ptr), o_dent = put(blob, P.d_ent), o_l = put(blob, P.l_pos);
     const size_t o_dcol = put(blob, P.d_col), o_lcol = put(blob, P.l_cols), o_pcol = put(blob, P.pos_col);
     const size_t o_hptr = put(blob, g->H.ptr), o_hcol = put(blob, g->H.col), o_thr = put(blob, P.thr);
@@ -346,6 +351,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     for (double p : g->priors) if (!(p < 0.5)) d.zero_ok = 0;
     d.kernel_id = vid;
     d.chk_idx = (const uint16_t *)(base + o_chk);
+    d.chk_word = (const uint16_t *)(base + o_chkw);
     d.var_deg = (const uint8_t *)(base + o_deg);
     d.lam = (const float *)(base + o_lam);
     d.d_ptr = (const int32_t *)(base + o_dptr);

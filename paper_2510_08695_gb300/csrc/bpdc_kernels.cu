@@ -182,12 +182,16 @@ template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC>
 struct Lane {
     static constexpr int kVmWords = (PVM * CVM + 31) / 32;
 
-    static constexpr int kAddrWords = (PCM * DCM + 1) / 2;
     static constexpr bool kWide = wide_slots(G, PVM, CVM);
     // shared byte address of each check edge's slot (the +inf word if none),
-    // two 16-bit values per word: the address itself when the block uses less
-    // than 64 KB of shared memory, else the word index in the group's region
+    // two 16-bit values per register.  The wide form (a group larger than
+    // 64 KB, one per SM, 64 registers per thread) keeps none: it reads the
+    // word index of the edge from the read-only table chk_word at each access
+    // (coalesced 2-byte loads), so that its registers do not spill.
+    static constexpr int kAddrWords = kWide ? 1 : (PCM * DCM + 1) / 2;
     uint32_t aw[kAddrWords];
+    const uint16_t *cw;        // wide form: this lane's column of chk_word
+    int cw_stride;             // wide form: dc * G
     uint32_t region_base;      // shared byte address of the group's region (wide form)
     uint32_t slot_base;        // shared byte address of slot 0
     uint32_t vm[kVmWords];     // bit (p*CVM + m): the variable at pass p has an m-th edge
@@ -205,10 +209,12 @@ struct Lane {
 
     __device__ __forceinline__ uint32_t addr(int p, int k) const
     {
-        const int n = p * DCM + k;
-        const uint32_t h = (n & 1) ? (aw[n >> 1] >> 16) : (aw[n >> 1] & 0xFFFFu);
-        if constexpr (kWide) return region_base + 4u * h;
-        return h;
+        if constexpr (kWide) {
+            return region_base + 4u * (uint32_t)__ldg(cw + p * cw_stride + k * G);
+        } else {
+            const int n = p * DCM + k;
+            return (n & 1) ? (aw[n >> 1] >> 16) : (aw[n >> 1] & 0xFFFFu);
+        }
     }
 
     __device__ void reload_lam(const DevGraph &g, int u)
@@ -228,20 +234,22 @@ struct Lane {
         region_base = slot_base - 4u * kMiscWords;
         this->slot_base = slot_base;
         cvalid = 0;
+        cw = g.chk_word + u;
+        cw_stride = g.dc * G;
 #pragma unroll
         for (int w = 0; w < kAddrWords; ++w) aw[w] = 0;
 #pragma unroll
         for (int p = 0; p < PCM; ++p) {
             if (p < g.pc && p * G + u < g.M) cvalid |= 1u << p;
+            if constexpr (!kWide) {
 #pragma unroll
-            for (int k = 0; k < DCM; ++k) {
-                uint32_t v = kNoEdge;
-                if (p < g.pc && k < g.dc) v = __ldg(g.chk_idx + ((size_t)p * g.dc + k) * G + u);
-                uint32_t a;
-                if constexpr (kWide) a = (v == kNoEdge) ? 2u : (uint32_t)kMiscWords + v;   // region words
-                else a = ((v == kNoEdge) ? inf_word : slot_base + 4u * v) & 0xFFFFu;
-                const int n = p * DCM + k;
-                aw[n >> 1] |= a << ((n & 1) * 16);
+                for (int k = 0; k < DCM; ++k) {
+                    uint32_t v = kNoEdge;
+                    if (p < g.pc && k < g.dc) v = __ldg(g.chk_idx + ((size_t)p * g.dc + k) * G + u);
+                    const uint32_t a = ((v == kNoEdge) ? inf_word : slot_base + 4u * v) & 0xFFFFu;
+                    const int n = p * DCM + k;
+                    aw[n >> 1] |= a << ((n & 1) * 16);
+                }
             }
         }
 #pragma unroll
@@ -333,8 +341,7 @@ struct Decoder {
                     if constexpr (RULE == 0) {
                         // normalized min-sum
                         float mn1 = f_inf(), mn2 = f_inf();
-#pragma unroll
-                        for (int k = 0; k < DCM; ++k) {
+                        auto gather = [&](int k) {
                             // unused slots point at the group's +inf word
                             const uint32_t b = lds32(ln.addr(p, k));
                             if constexpr (kHold) qb[k] = b;
@@ -342,6 +349,13 @@ struct Decoder {
                             const float av = fabsf(__uint_as_float(b));
                             mn2 = fminf(mn2, fmaxf(mn1, av));
                             mn1 = fminf(mn1, av);
+                        };
+                        if constexpr (kHold) {
+#pragma unroll
+                            for (int k = 0; k < DCM; ++k) gather(k);
+                        } else {   // long rows: bounded unrolling keeps few loads in flight
+#pragma unroll 5
+                            for (int k = 0; k < DCM; ++k) gather(k);
                         }
                         unsat |= S;
                         if (scatter) {
@@ -352,8 +366,7 @@ struct Decoder {
                             uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap)) ^ Sm;
                             uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap)) ^ Sm;
                             if (RC && !live) m1 = m2 = 0x7F800000u;   // idle check: writes +inf back
-#pragma unroll
-                            for (int k = 0; k < DCM; ++k) {
+                            auto put = [&](int k) {
                                 const uint32_t a = ln.addr(p, k);
                                 uint32_t qk;
                                 if constexpr (kHold) qk = qb[k];
@@ -362,6 +375,13 @@ struct Decoder {
                                 const uint32_t out = (is_min ? m2 : m1) ^ (qk & 0x80000000u);
                                 if (RC) sts32(a, out);
                                 else sts32_if(a, out, a != ln.inf_addr);
+                            };
+                            if constexpr (kHold) {
+#pragma unroll
+                                for (int k = 0; k < DCM; ++k) put(k);
+                            } else {
+#pragma unroll 5
+                                for (int k = 0; k < DCM; ++k) put(k);
                             }
                         }
                     } else {
