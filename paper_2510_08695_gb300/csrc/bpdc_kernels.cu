@@ -159,6 +159,15 @@ __device__ __forceinline__ uint32_t lds32(uint32_t a)
     return v;
 }
 
+// The same load typed as a float, so that |x| folds into the compare and
+// min / max instructions as an operand modifier instead of a separate mask.
+__device__ __forceinline__ float ldsf(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+
 __device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
 {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v));
@@ -317,6 +326,10 @@ struct Decoder {
     // initial messages, visible to the whole group.  Returns whether the hard
     // decision reproduced the syndrome; iters = iterations used; hd = hard
     // decision bits per variable pass.
+    // FAST: every check and variable pass of the variant is occupied and no
+    // posterior is written, so the per-pass guards compile away (the common
+    // case of a graph packed for its own variant; identical arithmetic).
+    template <bool FAST>
     static __device__ __forceinline__ bool run(const DevGraph &g, const L &ln, const Group<G> &grp,
                                                uint32_t sbits, uint32_t &hd, int &iters, float *post_row)
     {
@@ -329,7 +342,7 @@ struct Decoder {
             // ---- check phase ----
 #pragma unroll
             for (int p = 0; p < PCM; ++p) {
-                if (p < g.pc) {
+                if (FAST || p < g.pc) {
                     const bool live = (ln.cvalid >> p) & 1u;
                     // rows of up to 16 edges keep the gathered q in registers for
                     // the scatter; longer rows read each q again before
@@ -341,12 +354,13 @@ struct Decoder {
                     if constexpr (RULE == 0) {
                         // normalized min-sum
                         float mn1 = f_inf(), mn2 = f_inf();
+                        float qf[kHold ? DCM : 1];
                         auto gather = [&](int k) {
                             // unused slots point at the group's +inf word
-                            const uint32_t b = lds32(ln.addr(p, k));
-                            if constexpr (kHold) qb[k] = b;
-                            S ^= b;   // bit 31: sign parity, bit 0: hard-decision parity
-                            const float av = fabsf(__uint_as_float(b));
+                            const float v = ldsf(ln.addr(p, k));
+                            if constexpr (kHold) qf[k] = v;
+                            S ^= __float_as_uint(v);   // bit 31: sign parity, bit 0: hard-decision parity
+                            const float av = fabsf(v);
                             mn2 = fminf(mn2, fmaxf(mn1, av));
                             mn1 = fminf(mn1, av);
                         };
@@ -368,11 +382,11 @@ struct Decoder {
                             if (RC && !live) m1 = m2 = 0x7F800000u;   // idle check: writes +inf back
                             auto put = [&](int k) {
                                 const uint32_t a = ln.addr(p, k);
-                                uint32_t qk;
-                                if constexpr (kHold) qk = qb[k];
-                                else qk = lds32(a);
-                                const bool is_min = fabsf(__uint_as_float(qk)) == mn1;
-                                const uint32_t out = (is_min ? m2 : m1) ^ (qk & 0x80000000u);
+                                float vk;
+                                if constexpr (kHold) vk = qf[k];
+                                else vk = ldsf(a);
+                                const bool is_min = fabsf(vk) == mn1;
+                                const uint32_t out = (is_min ? m2 : m1) ^ (__float_as_uint(vk) & 0x80000000u);
                                 if (RC) sts32(a, out);
                                 else sts32_if(a, out, a != ln.inf_addr);
                             };
@@ -460,7 +474,7 @@ struct Decoder {
             uint32_t nhd = 0;
 #pragma unroll
             for (int p = 0; p < PVM; ++p) {
-                if (p < g.pv) {
+                if (FAST || p < g.pv) {
                     const uint32_t base = ln.lane_base + p * kPass;
                     float r[CVM];
 #pragma unroll
@@ -493,7 +507,7 @@ struct Decoder {
                         if (CMIN > 0) sts32(base, lv);
                         else sts32_if(base, lv, ln.has(p, 0));
                     }
-                    if (post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = Lp;
+                    if (!FAST && post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = Lp;
                 }
             }
             hd = nhd & ln.vvalid;
@@ -614,7 +628,9 @@ struct Decoder {
                     hd = init(g, ln, u, post_row);
                     grp.sync();
                     int iters = 0;
-                    const bool ok = run(g, ln, grp, sbits, hd, iters, post_row);
+                    const bool ok = (g.pc == PCM && g.pv == PVM && !post_row)
+                                        ? run<true>(g, ln, grp, sbits, hd, iters, post_row)
+                                        : run<false>(g, ln, grp, sbits, hd, iters, post_row);
                     if (second) it2 = iters; else it1 = iters;
                     if (ok) { st = second ? 1 : 0; break; }
                     if (second || cut_in || !g.dc_enable) { st = 2; break; }
