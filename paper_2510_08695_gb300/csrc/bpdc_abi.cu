@@ -215,9 +215,19 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
         for (int a = g.H.ptr[i]; a < g.H.ptr[i + 1]; ++a)
             P.chk_idx[((size_t)p * P.dc + lay.edge_round[a]) * G + u] = (uint16_t)edge_slot[a];
     }
-    P.chk_word.resize(P.chk_idx.size());
-    for (size_t k = 0; k < P.chk_idx.size(); ++k)
-        P.chk_word[k] = P.chk_idx[k] == kNoEdge ? (uint16_t)2 : (uint16_t)(12 + P.chk_idx[k]);   // 12 misc words
+    // the same edges as word indices of the group's region (12 misc words
+    // first; 2 = the +inf word), with the variant's full row width per pass
+    // so that a kernel reads every entry of its compile-time width in bounds
+    {
+        const int dcw = std::max(v.dc_max, P.dc);
+        P.chk_word.assign((size_t)P.pc * dcw * G, (uint16_t)2);
+        for (int p = 0; p < P.pc; ++p)
+            for (int k = 0; k < P.dc; ++k)
+                for (int u = 0; u < G; ++u) {
+                    const uint16_t e = P.chk_idx[((size_t)p * P.dc + k) * G + u];
+                    if (e != kNoEdge) P.chk_word[((size_t)p * dcw + k) * G + u] = (uint16_t)(12 + e);
+                }
+    }
     P.var_deg.assign((size_t)npos, 0xFF);   // 0xFF: no variable at this position
     P.lam.assign((size_t)npos, std::numeric_limits<float>::infinity());
     P.pos_col.assign((size_t)npos, -1);

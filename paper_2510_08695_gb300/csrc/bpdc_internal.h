@@ -50,8 +50,9 @@ struct DevGraph {
     int32_t w_T;
     float w_clip;
     const uint16_t *chk_idx;     // [pc][dc][G] message slot of the check's k-th edge, or kNoEdge
-    const uint16_t *chk_word;    // [pc][dc][G] the same as a word index of the group's region (the
-                                 // +inf word, 2, for none): read per access by the wide kernels
+    const uint16_t *chk_word;    // [pc][variant row width][G] the same as word indices of the group's
+                                 // region (the +inf word, 2, for none and for padding): read per
+                                 // access by the wide kernels
     const uint8_t *var_deg;      // [pv][G] degree of the variable (0 past N)
     const float *lam;            // [pv][G] prior LLR ln((1-p)/p)
     const int32_t *d_ptr;        // [Md+1] rows of D

@@ -199,8 +199,7 @@ struct Lane {
     // (coalesced 2-byte loads), so that its registers do not spill.
     static constexpr int kAddrWords = kWide ? 1 : (PCM * DCM + 1) / 2;
     uint32_t aw[kAddrWords];
-    const uint16_t *cw;        // wide form: this lane's column of chk_word
-    int cw_stride;             // wide form: dc * G
+    const uint16_t *cw;        // wide form: this lane's column of chk_word ([pc][DCM][G])
     uint32_t region_base;      // shared byte address of the group's region (wide form)
     uint32_t slot_base;        // shared byte address of slot 0
     uint32_t vm[kVmWords];     // bit (p*CVM + m): the variable at pass p has an m-th edge
@@ -219,7 +218,7 @@ struct Lane {
     __device__ __forceinline__ uint32_t addr(int p, int k) const
     {
         if constexpr (kWide) {
-            return region_base + 4u * (uint32_t)__ldg(cw + p * cw_stride + k * G);
+            return region_base + 4u * (uint32_t)__ldg(cw + (p * DCM + k) * G);
         } else {
             const int n = p * DCM + k;
             return (n & 1) ? (aw[n >> 1] >> 16) : (aw[n >> 1] & 0xFFFFu);
@@ -244,7 +243,6 @@ struct Lane {
         this->slot_base = slot_base;
         cvalid = 0;
         cw = g.chk_word + u;
-        cw_stride = g.dc * G;
 #pragma unroll
         for (int w = 0; w < kAddrWords; ++w) aw[w] = 0;
 #pragma unroll

@@ -257,6 +257,33 @@ def test_layouts_give_identical_results(pkg, name):
         assert (a == b).all() or (k == "posterior_llr" and bool(((a == b) | (a.isnan() & b.isnan())).all())), k
 
 
+@pytest.mark.parametrize("name", ["bb72", "bb144", "hgp"])
+def test_every_variant_gives_identical_results(pkg, name):
+    """Every compiled kernel variant that accepts a graph (as the autotuner
+    tries them, including the circuit-level one on small codes) decodes it
+    bit-identically: min-sum takes order-free minima, and each variable sums
+    its edges in ascending check order whatever the variant."""
+    P = {"bb72": lambda: bi.bb_problem("bb72", 0.06), "bb144": lambda: bi.bb_problem("bb144", 0.07),
+         "hgp": lambda: bi.hgp_problem(0.06)}[name]()
+    _, s, o = sample_shots(P, SEED + 22, 0, 1200 if P.N < 1000 else 300)
+    g = pkg.Graph.from_problem(P)
+    ks = g.kernels()
+    assert len(ks) >= 2
+    outs = {}
+    for k in ks:
+        g.set_kernel(k)
+        outs[k] = g.decode(to_dev(s), 0, obs_true=to_dev(o))
+    g.sync_status()
+    k0 = ks[0]
+    for k in ks[1:]:
+        for key in ("corrections", "status", "logical_flips", "iterations"):
+            assert torch_equal(outs[k][key], outs[k0][key]), (k, key)
+
+
+def torch_equal(a, b):
+    return bool((a == b).all())
+
+
 def test_decode_multi_equals_single(pkg):
     import torch
     probs = [bi.bb_problem("bb72", 0.04), bi.bb_problem("bb144", 0.05), bi.hgp_problem(0.05),
