@@ -246,6 +246,8 @@ def main():
     ap.add_argument("--only", choices=CODES + [CIRCUIT_CASE], default=None,
                     help="restrict the workload to one code (small profiling cases; not a bench line)")
     ap.add_argument("--p", type=float, default=None, help="restrict the workload to one error rate")
+    ap.add_argument("--kernel", type=int, default=None,
+                    help="pin this kernel variant for every code instead of autotuning (profiling cases)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -287,7 +289,7 @@ def main():
     # points of the code take the fastest
     from paper_2510_08695_gb300.autotune import autotune
     tuned = {}
-    for code in sorted({b["code"] for b in batches}):
+    for code in sorted({b["code"] for b in batches} if args.kernel is None else ()):
         probe = max((b for b in batches if b["code"] == code), key=lambda b: b["p"])
         n = min(20000, spp)
         res = autotune(probe["graph"], probe["syndromes"][:n].contiguous(), probe["shot_offset"])
@@ -295,6 +297,10 @@ def main():
             if b["code"] == code:
                 b["graph"].set_kernel(res["best"])
         tuned[code] = {"kernel": res["best"], "ms_per_variant": {str(k): round(v, 3) for k, v in res["ms"].items()}}
+    if args.kernel is not None:
+        for b in batches:
+            b["graph"].set_kernel(args.kernel)
+        tuned = {code: {"kernel": args.kernel, "pinned": True} for code in {b["code"] for b in batches}}
     torch.cuda.synchronize()
     groups = {}
     for b in batches:
@@ -349,8 +355,8 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     shots_per_step = len(batches) * spp * world
-    if args.only or args.p is not None:
-        line_note = "restricted workload (profiling case)"
+    if args.only or args.p is not None or args.kernel is not None:
+        line_note = "restricted workload or pinned kernel variant (profiling case)"
     else:
         line_note = None
     value = shots_per_step * args.steps / (ms / 1e3)
