@@ -168,6 +168,14 @@ __device__ __forceinline__ float ldsf(uint32_t a)
     return v;
 }
 
+// Minimum of three floats in one instruction (sm_100 and later).
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 __device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
 {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v));
@@ -192,12 +200,15 @@ struct Lane {
     static constexpr int kVmWords = (PVM * CVM + 31) / 32;
 
     static constexpr bool kWide = wide_slots(G, PVM, CVM);
-    // shared byte address of each check edge's slot (the +inf word if none),
-    // two 16-bit values per register.  The wide form (a group larger than
-    // 64 KB, one per SM, 64 registers per thread) keeps none: it reads the
-    // word index of the edge from the read-only table chk_word at each access
-    // (coalesced 2-byte loads), so that its registers do not spill.
-    static constexpr int kAddrWords = kWide ? 1 : (PCM * DCM + 1) / 2;
+    // shared byte address of each check edge's slot (the +inf word if none):
+    // one register per edge when a lane has at most 40 check edges (no
+    // unpacking at each access), else two 16-bit values per register.  The
+    // wide form (a group larger than 64 KB, one per SM, 64 registers per
+    // thread) keeps none: it reads the word index of the edge from the
+    // read-only table chk_word at each access (coalesced 2-byte loads), so
+    // that its registers do not spill.
+    static constexpr bool kFullAddr = !kWide && PCM * DCM <= 40;
+    static constexpr int kAddrWords = kWide ? 1 : kFullAddr ? PCM * DCM : (PCM * DCM + 1) / 2;
     uint32_t aw[kAddrWords];
     const uint16_t *cw;        // wide form: this lane's column of chk_word ([pc][DCM][G])
     uint32_t region_base;      // shared byte address of the group's region (wide form)
@@ -221,7 +232,8 @@ struct Lane {
             return region_base + 4u * (uint32_t)__ldg(cw + (p * DCM + k) * G);
         } else {
             const int n = p * DCM + k;
-            return (n & 1) ? (aw[n >> 1] >> 16) : (aw[n >> 1] & 0xFFFFu);
+            if constexpr (kFullAddr) return aw[n];
+            else return (n & 1) ? (aw[n >> 1] >> 16) : (aw[n >> 1] & 0xFFFFu);
         }
     }
 
@@ -255,7 +267,8 @@ struct Lane {
                     if (p < g.pc && k < g.dc) v = __ldg(g.chk_idx + ((size_t)p * g.dc + k) * G + u);
                     const uint32_t a = ((v == kNoEdge) ? inf_word : slot_base + 4u * v) & 0xFFFFu;
                     const int n = p * DCM + k;
-                    aw[n >> 1] |= a << ((n & 1) * 16);
+                    if constexpr (kFullAddr) aw[n] = a;
+                    else aw[n >> 1] |= a << ((n & 1) * 16);
                 }
             }
         }
@@ -341,7 +354,8 @@ struct Decoder {
 #pragma unroll
             for (int p = 0; p < PCM; ++p) {
                 if (FAST || p < g.pc) {
-                    const bool live = (ln.cvalid >> p) & 1u;
+                    // on the fast path every check pass but the last is full
+                    const bool live = (FAST && p < PCM - 1) || ((ln.cvalid >> p) & 1u);
                     // rows of up to 16 edges keep the gathered q in registers for
                     // the scatter; longer rows read each q again before
                     // overwriting it (one more load per edge, no register array)
@@ -363,8 +377,27 @@ struct Decoder {
                             mn1 = fminf(mn1, av);
                         };
                         if constexpr (kHold) {
+                            // edges in pairs: with lo <= hi the pair's
+                            // smallest two, the second minimum of the four
+                            // values {mn1 <= mn2, lo, hi} is
+                            // min(mn2, max(mn1, lo), hi)
+                            auto gather2 = [&](int k, bool first) {
+                                const float va = ldsf(ln.addr(p, k)), vb = ldsf(ln.addr(p, k + 1));
+                                qf[k] = va;
+                                qf[k + 1] = vb;
+                                S ^= __float_as_uint(va) ^ __float_as_uint(vb);
+                                const float lo = fminf(fabsf(va), fabsf(vb)), hi = fmaxf(fabsf(va), fabsf(vb));
+                                if (first) {
+                                    mn1 = lo;
+                                    mn2 = hi;
+                                } else {
+                                    mn2 = fmin3(mn2, fmaxf(mn1, lo), hi);
+                                    mn1 = fminf(mn1, lo);
+                                }
+                            };
 #pragma unroll
-                            for (int k = 0; k < DCM; ++k) gather(k);
+                            for (int k = 0; k + 1 < DCM; k += 2) gather2(k, k == 0);
+                            if (DCM & 1) gather(DCM - 1);
                         } else {   // long rows: bounded unrolling keeps few loads in flight
 #pragma unroll 5
                             for (int k = 0; k < DCM; ++k) gather(k);
