@@ -18,8 +18,12 @@
 //      with more than dc edges in a group is split into virtual nodes of at
 //      most dc edges, whose copies then share rounds (unavoidable conflicts).
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "bpdc_internal.h"
@@ -46,44 +50,80 @@ void assign_banks(int M, int N, const std::vector<int32_t> &row_ptr, const std::
     const int ng = (M + 31) / 32;
     std::vector<int> d(ng, 0);
     for (int i = 0; i < M; ++i) d[i / 32] = std::max(d[i / 32], row_ptr[i + 1] - row_ptr[i]);
-    // groups touched by each variable, with multiplicity
-    std::vector<std::vector<int>> vg(N);
+    // groups touched by each variable, once each, with the number of edges
+    std::vector<std::vector<std::pair<int, int>>> vg(N);
     for (int i = 0; i < M; ++i)
-        for (int a = row_ptr[i]; a < row_ptr[i + 1]; ++a) vg[col[a]].push_back(i / 32);
+        for (int a = row_ptr[i]; a < row_ptr[i + 1]; ++a) {
+            auto &l = vg[col[a]];
+            if (!l.empty() && l.back().first == i / 32) l.back().second++;
+            else l.emplace_back(i / 32, 1);
+        }
+    // variables of each group (with multiplicity), for the annealing
+    std::vector<std::vector<int>> gv(ng);
+    for (int i = 0; i < M; ++i)
+        for (int a = row_ptr[i]; a < row_ptr[i + 1]; ++a) gv[i / 32].push_back(col[a]);
     bank.resize(N);
     for (int j = 0; j < N; ++j) bank[j] = j % 32;
     std::vector<int> n((size_t)ng * 32, 0);
     for (int j = 0; j < N; ++j)
-        for (int g : vg[j]) n[(size_t)g * 32 + bank[j]]++;
+        for (auto gc : vg[j]) n[(size_t)gc.first * 32 + bank[j]] += gc.second;
     std::vector<std::vector<int>> members(32);
-    for (int j = 0; j < N; ++j) members[bank[j]].push_back(j);
+    std::vector<int> slot_in(N);
+    for (int j = 0; j < N; ++j) {
+        slot_in[j] = (int)members[bank[j]].size();
+        members[bank[j]].push_back(j);
+    }
     auto over = [&](int g, int x) { return std::max(0, x - d[g]); };
     // cost change of moving j from b0 to b (n unchanged)
     auto delta = [&](int j, int b0, int b) {
         int dl = 0;
-        for (size_t t = 0; t < vg[j].size(); ++t) {
-            const int g = vg[j][t];
-            bool first = true;
-            for (size_t s = 0; s < t; ++s) first &= vg[j][s] != g;
-            if (!first) continue;
-            int c = 0;
-            for (int h : vg[j]) c += h == g;
+        for (auto gc : vg[j]) {
+            const int g = gc.first, c = gc.second;
             const int x0 = n[(size_t)g * 32 + b0], x1 = n[(size_t)g * 32 + b];
             dl += over(g, x0 - c) - over(g, x0) + over(g, x1 + c) - over(g, x1);
         }
         return dl;
     };
     auto move = [&](int j, int b0, int b) {
-        for (int g : vg[j]) {
-            n[(size_t)g * 32 + b0]--;
-            n[(size_t)g * 32 + b]++;
+        for (auto gc : vg[j]) {
+            n[(size_t)gc.first * 32 + b0] -= gc.second;
+            n[(size_t)gc.first * 32 + b] += gc.second;
         }
         auto &m0 = members[b0];
-        m0.erase(std::find(m0.begin(), m0.end(), j));
+        const int last = m0.back();
+        m0[slot_in[j]] = last;
+        slot_in[last] = slot_in[j];
+        m0.pop_back();
+        slot_in[j] = (int)members[b].size();
         members[b].push_back(j);
         bank[j] = b;
     };
+    // best move of j out of b0 (into a bank with room) or swap with a sampled
+    // member of a full bank; returns the cost change, bt / jt the choice
     Rng rng(2510);
+    auto best_move = [&](int j, int b0, int swaps, int &bt, int &jt) {
+        int best = 1 << 30;
+        bt = jt = -1;
+        for (int b = 0; b < 32; ++b) {
+            if (b == b0) continue;
+            if ((int)members[b].size() < cap) {
+                const int dl = delta(j, b0, b);
+                if (dl < best || (dl == best && (rng.next() & 1))) { best = dl; bt = b; jt = -1; }
+            } else {
+                const auto &mb = members[b];
+                for (int s = 0; s < swaps && !mb.empty(); ++s) {
+                    const int j2 = mb[rng.next() % mb.size()];
+                    const int d1 = delta(j, b0, b);
+                    move(j, b0, b);
+                    const int d2 = delta(j2, b, b0);
+                    move(j, b, b0);
+                    if (d1 + d2 < best || (d1 + d2 == best && (rng.next() & 1))) { best = d1 + d2; bt = b; jt = j2; }
+                }
+            }
+        }
+        return best;
+    };
+    // 1. descent: every variable in turn takes its best strictly improving move
     std::vector<int> order(N);
     std::iota(order.begin(), order.end(), 0);
     for (int round = 0; round < 60; ++round) {
@@ -91,25 +131,8 @@ void assign_banks(int M, int N, const std::vector<int32_t> &row_ptr, const std::
         int improved = 0;
         for (int j : order) {
             const int b0 = bank[j];
-            int best = 0, bt = -1, jt = -1;
-            for (int b = 0; b < 32; ++b) {
-                if (b == b0) continue;
-                if ((int)members[b].size() < cap) {
-                    const int dl = delta(j, b0, b);
-                    if (dl < best) { best = dl; bt = b; jt = -1; }
-                } else {
-                    const auto &mb = members[b];
-                    for (int s = 0; s < 6 && !mb.empty(); ++s) {
-                        const int j2 = mb[rng.next() % mb.size()];
-                        const int d1 = delta(j, b0, b);
-                        move(j, b0, b);
-                        const int d2 = delta(j2, b, b0);
-                        move(j, b, b0);
-                        if (d1 + d2 < best) { best = d1 + d2; bt = b; jt = j2; }
-                    }
-                }
-            }
-            if (bt >= 0) {
+            int bt, jt;
+            if (best_move(j, b0, 6, bt, jt) < 0) {
                 move(j, b0, bt);
                 if (jt >= 0) move(jt, bt, b0);
                 ++improved;
@@ -117,6 +140,50 @@ void assign_banks(int M, int N, const std::vector<int32_t> &row_ptr, const std::
         }
         if (!improved) break;
     }
+    // 2. simulated annealing aimed at the overloaded (group, bank) cells: a
+    // variable of such a cell takes its best move even when that raises the
+    // overflow, with probability exp(-increase / T) under a falling
+    // temperature; the best assignment seen is kept.  The budget grows with
+    // the number of variables (deterministic: fixed seed and iteration count).
+    long cost = 0;
+    for (int g = 0; g < ng; ++g)
+        for (int b = 0; b < 32; ++b) cost += over(g, n[(size_t)g * 32 + b]);
+    long best_cost = cost;
+    std::vector<int> best_bank = bank;
+    const long iters = std::min<long>(3000000L, 400L * N);
+    const double T0 = 0.7;
+    std::vector<int> hot;
+    for (long it = 0; it < iters && cost > 0; ++it) {
+        if ((it & 255) == 0 || hot.empty()) {
+            hot.clear();
+            for (int c = 0; c < ng * 32; ++c)
+                if (n[c] > d[c / 32]) hot.push_back(c);
+            if (hot.empty()) break;
+        }
+        const int cell = hot[rng.next() % hot.size()];
+        const int g = cell / 32, b0 = cell % 32;
+        if (n[cell] <= d[g]) continue;
+        int j = -1;
+        for (int tries = 0; tries < 64 && j < 0; ++tries) {
+            const int jj = gv[g][rng.next() % gv[g].size()];
+            if (bank[jj] == b0) j = jj;
+        }
+        if (j < 0) continue;
+        int bt, jt;
+        const int dl = best_move(j, b0, 16, bt, jt);
+        if (bt < 0) continue;
+        const double T = T0 * (1.0 - (double)it / (double)iters) + 1e-3;
+        if (dl <= 0 || (double)(rng.next() & 0xFFFF) * (1.0 / 65536.0) < std::exp(-dl / T)) {
+            move(j, b0, bt);
+            if (jt >= 0) move(jt, bt, b0);
+            cost += dl;
+            if (cost < best_cost) {
+                best_cost = cost;
+                best_bank = bank;
+            }
+        }
+    }
+    bank = best_bank;
 }
 
 // Konig colouring of one group's bipartite multigraph; left = checks (local
@@ -166,8 +233,65 @@ std::vector<int> color_group(int nl, int nr, int D, const std::vector<std::pair<
 
 }  // namespace
 
+namespace {
+
+// Planned layouts of this process, keyed by the check matrix and the variant
+// shape: graphs of one code at several error rates, and the autotuner's
+// repeated switches between variants, plan each layout once.  Bounded: the
+// cache is emptied when it holds 32 layouts.
+struct LayoutKey {
+    uint64_t hash;
+    int M, N, G, npos, dc;
+    bool operator<(const LayoutKey &o) const
+    {
+        return std::tie(hash, M, N, G, npos, dc) < std::tie(o.hash, o.M, o.N, o.G, o.npos, o.dc);
+    }
+};
+
+uint64_t fnv1a(const std::vector<int32_t> &a, uint64_t h)
+{
+    for (int32_t v : a) {
+        for (int s = 0; s < 32; s += 8) {
+            h ^= (uint64_t)((uint32_t)v >> s) & 0xFFu;
+            h *= 0x100000001B3ull;
+        }
+    }
+    return h;
+}
+
+void plan_layout_uncached(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col,
+                          int G, int npos, int dc, bool optimize, Layout &out);
+
+}  // namespace
+
 void plan_layout(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col, int G,
                  int npos, int dc, bool optimize, Layout &out)
+{
+    if (!optimize || G % 32 != 0) {
+        plan_layout_uncached(M, N, row_ptr, col, G, npos, dc, optimize, out);
+        return;
+    }
+    static std::mutex mu;
+    static std::map<LayoutKey, Layout> cache;
+    const LayoutKey key{fnv1a(col, fnv1a(row_ptr, 0xCBF29CE484222325ull)), M, N, G, npos, dc};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            out = it->second;
+            return;
+        }
+    }
+    plan_layout_uncached(M, N, row_ptr, col, G, npos, dc, optimize, out);
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() >= 32) cache.clear();
+    cache.emplace(key, out);
+}
+
+namespace {
+
+void plan_layout_uncached(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col,
+                          int G, int npos, int dc, bool optimize, Layout &out)
 {
     out.pos_of_var.assign(N, -1);
     out.var_at_pos.assign(npos, -1);
@@ -215,5 +339,7 @@ void plan_layout(int M, int N, const std::vector<int32_t> &row_ptr, const std::v
         for (size_t t = 0; t < edges.size(); ++t) out.edge_round[eid[t]] = c[t];
     }
 }
+
+}  // namespace
 
 }  // namespace bpdc

@@ -45,4 +45,6 @@ def test_layout_is_valid_and_cuts_conflicts(name, G):
     assert (pos0 == np.arange(N)).all()
     w_opt, ideal = wavefronts(H, pos, rnd)
     w_nat, _ = wavefronts(H, pos0, rnd0)
-    assert w_opt < 0.8 * w_nat and w_opt <= 1.5 * ideal, (w_opt, w_nat, ideal)
+    # within 10 % of one wavefront per round (HGP-2500, whose groups need
+    # exactly 7 edges in every bank, keeps an overflow of about 18 edges)
+    assert w_opt < 0.6 * w_nat and w_opt <= 1.1 * ideal, (w_opt, w_nat, ideal)
