@@ -353,8 +353,10 @@ struct Decoder {
             // ---- check phase ----
 #pragma unroll
             for (int p = 0; p < PCM; ++p) {
-                if (FAST || p < g.pc) {
-                    // on the fast path every check pass but the last is full
+                // on the fast path every check pass but the last is full, and
+                // lanes without a check in the last pass skip it (their edges
+                // all point at the +inf word, which keeps its value)
+                if (FAST ? (p < PCM - 1 || ((ln.cvalid >> p) & 1u)) : p < g.pc) {
                     const bool live = (FAST && p < PCM - 1) || ((ln.cvalid >> p) & 1u);
                     // rows of up to 16 edges keep the gathered q in registers for
                     // the scatter; longer rows read each q again before
