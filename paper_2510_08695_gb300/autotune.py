@@ -5,19 +5,22 @@ checks and variables each thread owns, the row and column weights they are
 specialised for, and their register budget (resident blocks per SM).  For a
 graph the autotuner times every variant that accepts it on a sample of shots
 (CUDA events on the current stream, after a warm-up launch) and keeps the
-fastest.  Results are identical for every variant; only the speed differs.
+fastest; the graph's automatically chosen variant stays unless another is
+more than ``margin`` faster, so that near-ties do not flip between runs.
+Results are identical for every variant; only the speed differs.
 """
 from __future__ import annotations
 
 
 def autotune(graph, syndromes, shot_offset: int = 0, reps: int = 2, persistent: bool = True,
-             verbose: bool = False) -> dict:
+             verbose: bool = False, margin: float = 0.02) -> dict:
     """Selects the fastest kernel variant for ``graph`` on ``syndromes``.
 
     Returns ``{"best": kernel_id, "ms": {kernel_id: ms per decode}}``.
     """
     import torch
     B = int(syndromes.shape[0])
+    incumbent = graph.info["kernel_id"]
     times = {}
     for k in graph.kernels():
         graph.set_kernel(k)
@@ -36,5 +39,7 @@ def autotune(graph, syndromes, shot_offset: int = 0, reps: int = 2, persistent: 
             print(f"kernel {k}: G={graph.info['threads_per_shot']} blocks/SM={graph.info['blocks_per_sm']} "
                   f"{times[k]:.3f} ms", flush=True)
     best = min(times, key=times.get)
+    if incumbent in times and times[best] > (1.0 - margin) * times[incumbent]:
+        best = incumbent
     graph.set_kernel(best)
     return {"best": best, "ms": times}

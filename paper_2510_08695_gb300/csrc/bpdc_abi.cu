@@ -288,9 +288,10 @@ size_t put(std::vector<char> &blob, const std::vector<T> &v)
 // Packs the graph for threads_per_shot G (0 = automatic) and uploads it.
 int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
 {
-    // automatic preference: one warp per shot for small graphs, then the
-    // 256- and 512-thread groups
-    static const int kOrder[] = {0, 12, 5, 11, 1, 3, 2, 4, 6, 13};
+    // automatic preference: one warp per shot for small graphs (3 blocks per
+    // SM before 4: the same speed with fewer spills), then the 256- and
+    // 512-thread groups
+    static const int kOrder[] = {7, 0, 12, 5, 11, 1, 3, 2, 4, 6, 13};
     Packed P{};
     int vid = -1;
     for (int id : kOrder) {

@@ -280,6 +280,21 @@ def test_every_variant_gives_identical_results(pkg, name):
             assert torch_equal(outs[k][key], outs[k0][key]), (k, key)
 
 
+def test_autotune_choice(pkg):
+    """The autotuner times every accepting variant, keeps the automatic one
+    within its margin and otherwise takes the fastest."""
+    from paper_2510_08695_gb300.autotune import autotune
+    P = bi.bb_problem("bb72", 0.06)
+    _, s, _ = sample_shots(P, SEED + 23, 0, 2000)
+    g = pkg.Graph.from_problem(P)
+    k0 = g.info["kernel_id"]
+    ks = g.kernels()
+    res = autotune(g, to_dev(s), 0, margin=1.0)
+    assert set(res["ms"]) == set(ks) and res["best"] == k0 and g.info["kernel_id"] == k0
+    res = autotune(g, to_dev(s), 0, margin=0.0)
+    assert res["best"] == min(res["ms"], key=res["ms"].get) and g.info["kernel_id"] == res["best"]
+
+
 def torch_equal(a, b):
     return bool((a == b).all())
 
