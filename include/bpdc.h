@@ -200,6 +200,26 @@ typedef struct {
  * on each batch.  Asynchronous on `stream`. */
 int bpdc_decode_multi(const bpdc_batch *batches, int32_t n_batches, void *stream);
 
+/* Decoding from host memory (the paper has no counterpart: this is the end-to-
+ * end path of a decoder fed by the host).  The same batch list as
+ * bpdc_decode_multi, except that syndromes and every output pointer
+ * (corrections, status, and if non-NULL logical_flips, obs_true, iterations)
+ * are HOST pointers; posterior_llr, counters and cut_in must be NULL
+ * (BPDC_ERR_UNSUPPORTED otherwise).  The library cuts every batch into pieces
+ * of at most chunk_shots shots (0: 262144) and runs each piece through a
+ * three-stage pipeline: copy its syndromes (and obs_true) into one of two
+ * device staging sets on a copy stream, decode it with one persistent launch
+ * on `stream`, copy its outputs back on a second copy stream, so that the
+ * copies of one piece overlap the decoding of its neighbours.  Page-locked
+ * host buffers are needed for that overlap (pageable ones give the same
+ * results with serialised copies).  The staging memory (two pieces at the
+ * widest graph's row widths) is allocated on demand and kept by the first
+ * batch's graph until it is destroyed.  Results equal those of
+ * bpdc_decode_multi (the tie-break hash keys on the global shot index).
+ * Synchronous: returns when every output is in host memory, also after an
+ * error; `stream` is left ordered after the last copy. */
+int bpdc_decode_host(const bpdc_batch *batches, int32_t n_batches, int64_t chunk_shots, void *stream);
+
 /* Allocation-free variant of bpdc_decode_multi (the paper has no counterpart:
  * this is an integration aid).  Some callers cannot allocate device memory
  * while they decode: a real-time decoding loop that must not stall on the

@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
         "bpdc_decode": (ctypes.c_int, [vp, i64, vp, u64, ctypes.POINTER(_Outputs), ctypes.c_int, vp]),
         "bpdc_decode_multi": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
         "bpdc_decode_multi_noalloc": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
+        "bpdc_decode_host": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, i64, vp]),
         "bpdc_cut_select": (ctypes.c_int, [vp, i64, vp, u64, vp, vp]),
         "bpdc_sample": (ctypes.c_int, [vp, i64, u64, u64, vp, vp, vp, vp]),
         "bpdc_graph_sync_status": (ctypes.c_int, [vp, vp]),
@@ -245,6 +246,17 @@ class Graph:
             out["posterior_llr"] = torch.empty((B, self.N), dtype=torch.float32, device=dev)
         return out
 
+    def alloc_host_outputs(self, B: int, iterations=True, logical=True):
+        """Page-locked host outputs for decode_host (same shapes as alloc_outputs)."""
+        import torch
+        out = dict(corrections=torch.empty((B, self.NW), dtype=torch.int32, pin_memory=True),
+                   status=torch.empty((B,), dtype=torch.uint8, pin_memory=True))
+        if logical:
+            out["logical_flips"] = torch.empty((B, max(self.KW, 1)), dtype=torch.int32, pin_memory=True)
+        if iterations:
+            out["iterations"] = torch.empty((B,), dtype=torch.int32, pin_memory=True)
+        return out
+
     def _outputs(self, out, obs_true=None, counters=None, cut_in=None) -> _Outputs:
         return _Outputs(_ptr(out["corrections"]), _ptr(out["status"]), _ptr(out.get("logical_flips")),
                         _ptr(obs_true), _ptr(out.get("iterations")), _ptr(out.get("posterior_llr")),
@@ -327,6 +339,29 @@ def decode_multi(items, stream=None):
     """
     lib = load()
     _check(lib.bpdc_decode_multi(_batches(items), len(items), _stream_ptr(stream)))
+
+
+def decode_host(items, chunk_shots: int = 0, stream=None):
+    """bpdc_decode_host: the decode of ``decode_multi`` from and into HOST
+    tensors (page-locked for copy / compute overlap), pipelined in pieces of
+    at most ``chunk_shots`` shots (0: the library's default).  ``items`` as for
+    decode_multi, with CPU tensors for syndromes, obs_true and every output;
+    synchronous."""
+    import torch
+    for it in items:
+        g, syn, out = it["graph"], it["syndromes"], it["out"]
+        B = int(syn.shape[0])
+        want = {"syndromes": (syn, (B, g.MW), torch.int32), "obs_true": (it.get("obs_true"), (B, max(g.KW, 1)), torch.int32),
+                "corrections": (out["corrections"], (B, g.NW), torch.int32), "status": (out["status"], (B,), torch.uint8),
+                "logical_flips": (out.get("logical_flips"), (B, max(g.KW, 1)), torch.int32),
+                "iterations": (out.get("iterations"), (B,), torch.int32)}
+        for name, (t, shape, dtype) in want.items():
+            if t is None:
+                continue
+            if t.is_cuda or not t.is_contiguous() or tuple(t.shape) != shape or t.dtype != dtype:
+                raise ValueError(f"decode_host: {name} must be a contiguous CPU {dtype} tensor of shape {shape}")
+    lib = load()
+    _check(lib.bpdc_decode_host(_batches(items), len(items), int(chunk_shots), _stream_ptr(stream)))
 
 
 def decode_multi_noalloc(items, stream=None):

@@ -56,6 +56,7 @@ struct DeviceGuard {
 };
 
 constexpr int kRing = BPDC_MAX_INFLIGHT;
+constexpr int64_t kHostChunk = 262144;   // default shots per piece of bpdc_decode_host
 constexpr int kMaxBatches = 32;
 constexpr int kMaxSmemPerBlock = 227 * 1024;
 
@@ -121,6 +122,13 @@ struct bpdc_graph_s {
     std::vector<float> w_host;   // learned weights [2][w_T][E] (CSR edge order), empty if none
     int w_T = 0;
     float w_clip = 0.0f;
+    // decoding from host buffers (bpdc_decode_host): two device staging sets,
+    // the copy streams, and the events that order copies against decodes
+    void *stage = nullptr;
+    size_t stage_set_bytes = 0;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_dec[2] = {}, ev_out[2] = {};
+    cudaEvent_t ev_entry = nullptr, ev_exit = nullptr;
     std::mutex mu;
 };
 
@@ -411,6 +419,16 @@ void graph_free(bpdc_graph_s *g)
 {
     for (int s = 0; s < kRing; ++s)
         if (g->ring[s].done) cudaEventDestroy(g->ring[s].done);
+    for (int k = 0; k < 2; ++k) {
+        if (g->ev_in[k]) cudaEventDestroy(g->ev_in[k]);
+        if (g->ev_dec[k]) cudaEventDestroy(g->ev_dec[k]);
+        if (g->ev_out[k]) cudaEventDestroy(g->ev_out[k]);
+    }
+    if (g->ev_entry) cudaEventDestroy(g->ev_entry);
+    if (g->ev_exit) cudaEventDestroy(g->ev_exit);
+    if (g->copy_in) cudaStreamDestroy(g->copy_in);
+    if (g->copy_out) cudaStreamDestroy(g->copy_out);
+    if (g->stage) cudaFree(g->stage);
     if (g->ring_mem) cudaFree(g->ring_mem);
     if (g->ring_host) cudaFreeHost(g->ring_host);
     if (g->arena) cudaFree(g->arena);
@@ -761,6 +779,145 @@ int bpdc_decode_multi(const bpdc_batch *batches, int32_t n, void *stream)
         int rc = enqueue(owner, s, cnt, total, vid, smem, true, (cudaStream_t)stream);
         if (rc != BPDC_OK) return rc;
     }
+    return BPDC_OK;
+}
+
+int bpdc_decode_host(const bpdc_batch *batches, int32_t n, int64_t chunk_shots, void *stream)
+{
+    if (n < 0 || (n > 0 && !batches)) return fail(BPDC_ERR_INVALID_ARG, "bad batch list");
+    if (chunk_shots < 0) return fail(BPDC_ERR_INVALID_ARG, "chunk_shots < 0");
+    if (n == 0) return BPDC_OK;
+    const int64_t chunk = chunk_shots > 0 ? chunk_shots : kHostChunk;
+    const int dev = batches[0].graph ? batches[0].graph->device : -1;
+    size_t mw = 1, nw = 1, kw = 1;
+    int64_t shots = 0;
+    for (int i = 0; i < n; ++i) {
+        const bpdc_batch &bt = batches[i];
+        if (!bt.graph) return fail(BPDC_ERR_INVALID_ARG, "batch %d has no graph", i);
+        if (bt.graph->device != dev) return fail(BPDC_ERR_INVALID_ARG, "graphs on different devices");
+        if (bt.B < 0) return fail(BPDC_ERR_INVALID_ARG, "batch %d: B < 0", i);
+        if (bt.B == 0) continue;
+        if (!bt.syndromes) return fail(BPDC_ERR_INVALID_ARG, "batch %d: syndromes NULL", i);
+        int rc = check_outputs(&bt.out);
+        if (rc != BPDC_OK) return rc;
+        if (bt.out.posterior_llr || bt.out.counters || bt.out.cut_in)
+            return fail(BPDC_ERR_UNSUPPORTED,
+                        "batch %d: bpdc_decode_host takes no posterior_llr, counters or cut_in", i);
+        mw = std::max(mw, (size_t)bt.graph->dg.MW);
+        nw = std::max(nw, (size_t)bt.graph->dg.NW);
+        kw = std::max(kw, (size_t)bt.graph->dg.KW);
+        shots += bt.B;
+    }
+    if (shots == 0) return BPDC_OK;
+    // one staging set: syndromes, obs_true, corrections, logical flips,
+    // iterations and status of `chunk` shots at the widest graph's row widths
+    const size_t rows = (size_t)std::min<int64_t>(chunk, shots);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_syn = 0, o_obs = o_syn + al(rows * mw * 4), o_cor = o_obs + al(rows * kw * 4);
+    const size_t o_lf = o_cor + al(rows * nw * 4), o_it = o_lf + al(rows * kw * 4), o_st = o_it + al(rows * 4);
+    const size_t set_bytes = o_st + al(rows);
+
+    bpdc_graph_s *owner = batches[0].graph;
+    std::lock_guard<std::mutex> lk(owner->mu);
+    DeviceGuard dgd(dev);
+    if (!dgd.ok) return fail(BPDC_ERR_CUDA, "cannot select device %d", dev);
+    cudaError_t e = cudaSuccess;
+    if (!owner->copy_in) e = cudaStreamCreateWithFlags(&owner->copy_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !owner->copy_out) e = cudaStreamCreateWithFlags(&owner->copy_out, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (!owner->ev_in[k]) e = cudaEventCreateWithFlags(&owner->ev_in[k], cudaEventDisableTiming);
+        if (e == cudaSuccess && !owner->ev_dec[k]) e = cudaEventCreateWithFlags(&owner->ev_dec[k], cudaEventDisableTiming);
+        if (e == cudaSuccess && !owner->ev_out[k]) e = cudaEventCreateWithFlags(&owner->ev_out[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && !owner->ev_entry) e = cudaEventCreateWithFlags(&owner->ev_entry, cudaEventDisableTiming);
+    if (e == cudaSuccess && !owner->ev_exit) e = cudaEventCreateWithFlags(&owner->ev_exit, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "host-decode streams and events");
+    if (owner->stage_set_bytes < set_bytes) {
+        // every earlier call returned after its copies, so the old staging is idle
+        if (owner->stage) cudaFree(owner->stage);
+        owner->stage = nullptr;
+        owner->stage_set_bytes = 0;
+        e = cudaMalloc(&owner->stage, 2 * set_bytes);
+        if (e != cudaSuccess)
+            return fail(BPDC_ERR_OOM, "host-decode staging of %zu bytes: %s", 2 * set_bytes, cudaGetErrorString(e));
+        owner->stage_set_bytes = set_bytes;
+    }
+    const cudaStream_t cs = (cudaStream_t)stream;
+    // the copies start after the work already queued on the caller's stream
+    e = cudaEventRecord(owner->ev_entry, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(owner->copy_in, owner->ev_entry, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(owner->copy_out, owner->ev_entry, 0);
+    int rc = e == cudaSuccess ? BPDC_OK : cuda_fail(e, "host-decode entry");
+
+    // pieces of at most `chunk` shots of each batch, alternating between the
+    // two staging sets: copy in (copy_in), decode (caller's stream), copy out
+    // (copy_out).  The copy-in of piece k waits until the decode of piece
+    // k - 2 has read its set; the decode of piece k waits for its inputs and
+    // until the outputs of piece k - 2 have left the set.
+    int64_t k = 0;
+    for (int i = 0; i < n && rc == BPDC_OK; ++i) {
+        const bpdc_batch &bt = batches[i];
+        const bpdc_graph_s *g = bt.graph;
+        const size_t MW = (size_t)g->dg.MW, NW = (size_t)g->dg.NW, KW = (size_t)g->dg.KW;
+        for (int64_t b0 = 0; b0 < bt.B && rc == BPDC_OK; b0 += chunk, ++k) {
+            const int64_t nb = std::min<int64_t>(chunk, bt.B - b0);
+            const int s = (int)(k & 1);
+            char *base = static_cast<char *>(owner->stage) + (size_t)s * owner->stage_set_bytes;
+            uint32_t *d_syn = reinterpret_cast<uint32_t *>(base + o_syn);
+            uint32_t *d_obs = reinterpret_cast<uint32_t *>(base + o_obs);
+            uint32_t *d_cor = reinterpret_cast<uint32_t *>(base + o_cor);
+            uint32_t *d_lf = reinterpret_cast<uint32_t *>(base + o_lf);
+            uint32_t *d_it = reinterpret_cast<uint32_t *>(base + o_it);
+            uint8_t *d_st = reinterpret_cast<uint8_t *>(base + o_st);
+            e = cudaStreamWaitEvent(owner->copy_in, owner->ev_dec[s], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_syn, bt.syndromes + (size_t)b0 * MW, (size_t)nb * MW * 4, cudaMemcpyDefault,
+                                    owner->copy_in);
+            if (e == cudaSuccess && bt.out.obs_true)
+                e = cudaMemcpyAsync(d_obs, bt.out.obs_true + (size_t)b0 * KW, (size_t)nb * KW * 4,
+                                    cudaMemcpyDefault, owner->copy_in);
+            if (e == cudaSuccess) e = cudaEventRecord(owner->ev_in[s], owner->copy_in);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, owner->ev_in[s], 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, owner->ev_out[s], 0);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "host-decode copy-in"); break; }
+            bpdc_outputs o{};
+            o.corrections = d_cor;
+            o.status = d_st;
+            o.logical_flips = bt.out.logical_flips ? d_lf : nullptr;
+            o.obs_true = bt.out.obs_true ? d_obs : nullptr;
+            o.iterations = bt.out.iterations ? d_it : nullptr;
+            const int slot = acquire_slot(owner);
+            fill_desc(owner->ring[slot].host_desc[0], g, nb, d_syn, bt.shot_offset + (uint64_t)b0, &o, 0);
+            rc = enqueue(owner, slot, 1, nb, g->variant, g->smem_bytes, true, cs);
+            if (rc != BPDC_OK) break;
+            e = cudaEventRecord(owner->ev_dec[s], cs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(owner->copy_out, owner->ev_dec[s], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(bt.out.corrections + (size_t)b0 * NW, d_cor, (size_t)nb * NW * 4,
+                                    cudaMemcpyDefault, owner->copy_out);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(bt.out.status + b0, d_st, (size_t)nb, cudaMemcpyDefault, owner->copy_out);
+            if (e == cudaSuccess && bt.out.logical_flips)
+                e = cudaMemcpyAsync(bt.out.logical_flips + (size_t)b0 * KW, d_lf, (size_t)nb * KW * 4,
+                                    cudaMemcpyDefault, owner->copy_out);
+            if (e == cudaSuccess && bt.out.iterations)
+                e = cudaMemcpyAsync(bt.out.iterations + b0, d_it, (size_t)nb * 4, cudaMemcpyDefault,
+                                    owner->copy_out);
+            if (e == cudaSuccess) e = cudaEventRecord(owner->ev_out[s], owner->copy_out);
+            if (e != cudaSuccess) rc = cuda_fail(e, "host-decode copy-out");
+        }
+    }
+    // synchronous: every copy has landed when the call returns (also after an
+    // error, so that no copy into the caller's buffers is still in flight);
+    // the caller's stream is left ordered after the last copy-out
+    cudaError_t e1 = cudaEventRecord(owner->ev_exit, owner->copy_out);
+    if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(cs, owner->ev_exit, 0);
+    const cudaError_t e2 = cudaStreamSynchronize(owner->copy_in);
+    const cudaError_t e3 = cudaStreamSynchronize(owner->copy_out);
+    const cudaError_t e4 = cudaStreamSynchronize(cs);
+    if (rc != BPDC_OK) return rc;
+    for (cudaError_t x : {e1, e2, e3, e4})
+        if (x != cudaSuccess) return cuda_fail(x, "host-decode completion");
     return BPDC_OK;
 }
 

@@ -107,6 +107,16 @@ def test_weighted_bp_calls_reject_a_null_graph(lib):
         == _bpdc.ERR_INVALID_ARG
 
 
+def test_host_decode_rejects_bad_arguments(lib):
+    """bpdc_decode_host checks its batch list before it touches a GPU."""
+    assert lib.bpdc_decode_host(None, 1, 0, None) == _bpdc.ERR_INVALID_ARG
+    assert lib.bpdc_decode_host(None, 0, 0, None) == 0
+    arr = (_bpdc._Batch * 1)()
+    arr[0].B = 4
+    assert lib.bpdc_decode_host(arr, 1, -1, None) == _bpdc.ERR_INVALID_ARG
+    assert lib.bpdc_decode_host(arr, 1, 0, None) == _bpdc.ERR_INVALID_ARG   # no graph
+
+
 def test_valid_problem_needs_a_device_or_succeeds(lib):
     H, L, D, p = _small()
     rc, out = _create(lib, H, L, D, p)
