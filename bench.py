@@ -108,9 +108,11 @@ def profiled_traffic(kernel_id: int, shots: int, edge_updates: int):
     text = open(src, "rb").read()
     # the device code and the variant table (everything before the host-side
     # kVariants array; host launch code below it does not change the kernels),
-    # without comments and blank lines
+    # without comments, blank lines and the checked build's guard blocks
     import re
     code = text[:text.index(b"static const Variant kVariants[]")].decode()
+    # the bounds checks of the checked build are not part of the timed kernel
+    code = re.sub(r"#ifdef BPDC_CHECKS\n.*?#endif\n", "", code, flags=re.S)
     code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", code, flags=re.S))
     code = "\n".join(line.rstrip() for line in code.splitlines() if line.strip())
     cur = hashlib.sha256(code.encode()).hexdigest()[:16]

@@ -53,6 +53,7 @@ extern "C" {
 #define BPDC_ERR_CUDA (-4)          /* a CUDA runtime call failed */
 #define BPDC_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
 #define BPDC_ERR_UNSUPPORTED (-6)   /* valid request the library does not implement */
+#define BPDC_ERR_CHECK (-7)         /* checked build: an index left its bounds (access skipped) */
 
 #define BPDC_MAX_INFLIGHT 64
 
@@ -264,6 +265,20 @@ int bpdc_sample(bpdc_graph_t g, int64_t B, uint64_t seed, uint64_t shot_offset,
  * error latched since the last call (BPDC_ERR_TIMEOUT, BPDC_ERR_CUDA), then
  * clears it. */
 int bpdc_graph_sync_status(bpdc_graph_t g, void *stream);
+
+/* Bounds checks (a debugging aid; the paper has none).  The library is also
+ * built as libbpdc_checked.so with -DBPDC_CHECKS: there the decode kernel
+ * compares every shared-memory message access with the block's dynamic shared
+ * memory and every read of its per-lane graph tables (check addresses, check
+ * words, variable positions, D rows, weights) and every indexed output or
+ * cut-mask write with the table's length.  The first violation on a device
+ * latches its site (1 shared load, 2 shared store, 3 check-address table,
+ * 4 check-word table, 5 position tables, 6 D rows, 7 output / cut-mask index,
+ * 8 weights) and index, and the access is skipped; nothing traps.  This call
+ * waits for the device, writes the latched site (0: none) and index, clears
+ * the latch and returns BPDC_ERR_CHECK if a check failed.  The normal library
+ * compiles no checks and returns BPDC_ERR_UNSUPPORTED. */
+int bpdc_check_status(int32_t device, int32_t *site, int64_t *index);
 
 /* Shared-memory bandwidth of device `device`, the roof of the decode kernels
  * (their messages stay in shared memory; one 4-byte load and one 4-byte store

@@ -30,6 +30,7 @@ class BpdcError(RuntimeError):
 
 
 ERR_INVALID_ARG, ERR_DIM_MISMATCH, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+ERR_CHECK = -7
 
 
 class _Csr(ctypes.Structure):
@@ -74,16 +75,18 @@ def declared_symbols() -> list[str]:
 
 
 def library_path() -> str:
-    return _build.LIB
+    """Path of the library load() uses (the checked build under BPDC_CHECKED=1)."""
+    return _build.LIB_CHECKED if os.environ.get("BPDC_CHECKED") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Loads libbpdc.so (building it first if needed)."""
+    """Loads libbpdc.so (building it first if needed); libbpdc_checked.so, the
+    bounds-checked debugging build, when the environment sets BPDC_CHECKED=1."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if build_if_missing and _build.stale():
+    path = library_path()
+    if build_if_missing and _build.stale(path):
         _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"libbpdc.so not built at {path}; run paper_2510_08695_gb300.build.build()")
@@ -108,6 +111,7 @@ def load(build_if_missing: bool = True):
         "bpdc_cut_select": (ctypes.c_int, [vp, i64, vp, u64, vp, vp]),
         "bpdc_sample": (ctypes.c_int, [vp, i64, u64, u64, vp, vp, vp, vp]),
         "bpdc_graph_sync_status": (ctypes.c_int, [vp, vp]),
+        "bpdc_check_status": (ctypes.c_int, [i32, _i32p, ctypes.POINTER(ctypes.c_int64)]),
         "bpdc_graph_set_weights": (ctypes.c_int, [vp, vp, i32, ctypes.c_float]),
         "bpdc_wbp_workspace_size": (ctypes.c_int, [vp, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]),
         "bpdc_wbp_forward": (ctypes.c_int, [vp, i64, vp, vp, i32, ctypes.c_float, i32, vp, vp, ctypes.c_size_t,
@@ -329,6 +333,18 @@ def _batches(items):
         arr[i].shot_offset = int(it.get("shot_offset", 0))
         arr[i].out = g._outputs(it["out"], it.get("obs_true"), it.get("counters"), it.get("cut_in"))
     return arr
+
+
+def check_status(device: int = 0):
+    """bpdc_check_status (checked build only): None if no bounds check failed
+    on ``device`` since the last call, else (site, index) of the first
+    failure; the latch is cleared.  Raises BpdcError in the normal build."""
+    site, index = ctypes.c_int32(), ctypes.c_int64()
+    rc = load().bpdc_check_status(int(device), ctypes.byref(site), ctypes.byref(index))
+    if rc == ERR_CHECK:
+        return site.value, index.value
+    _check(rc)
+    return None
 
 
 def decode_multi(items, stream=None):

@@ -2,8 +2,10 @@
 
 ``python -m paper_2510_08695_gb300.build`` or ``build()``: every ``.cu`` file
 under ``csrc/`` is compiled by nvcc in parallel, then linked into
-``_build/libbpdc.so``.  Rebuilds only when a source or header is newer than
-the library.
+``_build/libbpdc.so``; the same sources compiled with ``-DBPDC_CHECKS`` give
+``_build/libbpdc_checked.so``, the bounds-checked debugging build (loaded
+instead when the environment sets BPDC_CHECKED=1).  Rebuilds only when a
+source or header is newer than the library.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbpdc.so")
+LIB_CHECKED = os.path.join(OUT, "libbpdc_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", f"-I{os.path.join(ROOT, 'include')}"]
@@ -36,29 +39,34 @@ def _inputs():
     return srcs, deps
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
     _, deps = _inputs()
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in deps + [__file__])
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not stale():
+    """Builds both libraries (all translation units of both in parallel)."""
+    todo = [(lib, sub, extra) for lib, sub, extra in ((LIB, "", []), (LIB_CHECKED, "checked", ["-DBPDC_CHECKS"]))
+            if force or stale(lib)]
+    if not todo:
         return LIB
-    os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
     srcs, _ = _inputs()
     procs = []
-    objs = []
-    for s in srcs:
-        o = os.path.join(OUT, os.path.basename(s) + ".o")
-        objs.append(o)
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o]
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        procs.append((s, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+    objs = {}
+    for lib, sub, extra in todo:
+        odir = os.path.join(OUT, sub)
+        os.makedirs(odir, exist_ok=True)
+        for s in srcs:
+            o = os.path.join(odir, os.path.basename(s) + ".o")
+            objs.setdefault(lib, []).append(o)
+            cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            procs.append((s, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
     errors = []
     for s, p in procs:
         out, _ = p.communicate()
@@ -68,9 +76,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(out, file=sys.stderr)
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+    for lib, _, _ in todo:
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs[lib]])
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -389,6 +389,13 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     d.w_T = P.wts.empty() ? 0 : g->w_T;
     d.w_clip = g->w_clip;
     d.err_flag = (int32_t *)(base + o_err);
+#ifdef BPDC_CHECKS
+    d.n_chk_idx = (int64_t)P.chk_idx.size();
+    d.n_chk_word = (int64_t)P.chk_word.size();
+    d.n_pos = (int64_t)P.pos_col.size();
+    d.n_d_ent = (int64_t)P.d_ent.size();
+    d.n_wts = (int64_t)P.wts.size();
+#endif
     g->variant = vid;
     g->groups_per_block = gpb;
     g->blocks_per_sm = bps;
@@ -1007,6 +1014,27 @@ int bpdc_graph_sync_status(bpdc_graph_t g, void *stream)
         return fail(flag, "device reported error %d", flag);
     }
     return BPDC_OK;
+}
+
+int bpdc_check_status(int32_t device, int32_t *site, int64_t *index)
+{
+    if (!site || !index) return fail(BPDC_ERR_INVALID_ARG, "bpdc_check_status: NULL output");
+#ifndef BPDC_CHECKS
+    (void)device;
+    return fail(BPDC_ERR_UNSUPPORTED, "bounds checks are compiled only into libbpdc_checked.so");
+#else
+    DeviceGuard dgd(device);
+    if (!dgd.ok) return fail(BPDC_ERR_CUDA, "cannot select device %d", device);
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "device synchronize");
+    int s = 0;
+    long long i = 0;
+    if (!check_status(&s, &i)) return fail(BPDC_ERR_CUDA, "bounds-check latch unreadable");
+    *site = s;
+    *index = (int64_t)i;
+    if (s != 0) return fail(BPDC_ERR_CHECK, "bounds check failed at site %d, index %lld", s, i);
+    return BPDC_OK;
+#endif
 }
 
 int bpdc_measure_smem_peak(int32_t device, int32_t reps, double *bytes_per_second, int32_t *num_sms)

@@ -68,6 +68,10 @@ struct DevGraph {
     const int32_t *c_edge;       // [E] edge ids (CSR order of H) by column, ascending check
     const float *lam_col;        // [N] prior LLR by column (weighted BP)
     int32_t *err_flag;           // latched device error code
+#ifdef BPDC_CHECKS
+    // entries of the tables the checked build compares indices with
+    int64_t n_chk_idx, n_chk_word, n_pos, n_d_ent, n_wts;
+#endif
 };
 
 // One batch of a decode launch (kept in device memory).
@@ -118,6 +122,9 @@ void plan_layout(int M, int N, const std::vector<int32_t> &row_ptr, const std::v
                  int npos, int dc, bool optimize, Layout &out);
 
 int num_variants();
+// Checked builds: the first failed bounds check since the last call (site 0:
+// none) and its index, then cleared.  Normal builds return false.
+bool check_status(int *site, long long *index);
 const Variant &variant(int id);
 // Occupancy query and launch of variant `id`.
 cudaError_t variant_attributes(int id, int smem_bytes, int *blocks_per_sm, int *regs);

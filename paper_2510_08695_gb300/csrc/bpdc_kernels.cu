@@ -48,6 +48,43 @@
 
 namespace bpdc {
 namespace {
+#ifdef BPDC_CHECKS
+// Checked build (libbpdc_checked.so): the first failed bounds check on the
+// device latches (site, index) here and the access is skipped; nothing traps.
+__device__ unsigned long long g_check[2];
+
+__device__ __forceinline__ void check_fail(int site, long long idx)
+{
+    if (atomicCAS(&g_check[0], 0ull, (unsigned long long)site) == 0ull) atomicExch(&g_check[1], (unsigned long long)idx);
+}
+
+__device__ __forceinline__ bool check_index(int site, long long idx, long long len)
+{
+    if (idx >= 0 && idx < len) return true;
+    check_fail(site, idx);
+    return false;
+}
+
+// a 4-byte access at shared address a lies inside the block's dynamic shared
+// memory and is aligned
+__device__ __forceinline__ bool smem_ok(uint32_t a, int site)
+{
+    extern __shared__ uint32_t smem_all[];
+    const uint32_t lo = (uint32_t)__cvta_generic_to_shared(smem_all);
+    uint32_t size;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(size));
+    if (a >= lo && a + 4u <= lo + size && (a & 3u) == 0u) return true;
+    check_fail(site, (long long)a - (long long)lo);
+    return false;
+}
+
+// the position j has a column and the column indexes a posterior row
+__device__ __forceinline__ bool post_ok(const DevGraph &g, long long j)
+{
+    return check_index(5, j, g.n_pos) && check_index(7, __ldg(g.pos_col + j), g.N);
+}
+#endif
+
 
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 
@@ -109,6 +146,9 @@ __device__ __forceinline__ void cut_rows(const DevGraph &g, uint64_t gshot, int 
 {
     for (int r = u; r < g.Md; r += G) {
         const int b0 = __ldg(g.d_ptr + r), b1 = __ldg(g.d_ptr + r + 1);
+#ifdef BPDC_CHECKS
+        if (b0 < b1 && (!check_index(6, b0, g.n_d_ent) || !check_index(6, b1 - 1, g.n_d_ent))) continue;
+#endif
         if (b0 == b1) continue;
         float lmax = -f_inf();
         for (int a = b0; a < b1; ++a) {
@@ -154,6 +194,9 @@ constexpr int kMiscWords = 12;
 
 __device__ __forceinline__ uint32_t lds32(uint32_t a)
 {
+#ifdef BPDC_CHECKS
+    if (!smem_ok(a, 1)) return 0u;
+#endif
     uint32_t v;
     asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
@@ -163,6 +206,9 @@ __device__ __forceinline__ uint32_t lds32(uint32_t a)
 // min / max instructions as an operand modifier instead of a separate mask.
 __device__ __forceinline__ float ldsf(uint32_t a)
 {
+#ifdef BPDC_CHECKS
+    if (!smem_ok(a, 1)) return 0.0f;
+#endif
     float v;
     asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
     return v;
@@ -178,6 +224,9 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
 
 __device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
 {
+#ifdef BPDC_CHECKS
+    if (!smem_ok(a, 2)) return;
+#endif
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v));
 }
 
@@ -185,6 +234,9 @@ __device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
 // emits one predicated store instead of a branch around the inline asm.
 __device__ __forceinline__ void sts32_if(uint32_t a, uint32_t v, bool pred)
 {
+#ifdef BPDC_CHECKS
+    if (pred && !smem_ok(a, 2)) return;
+#endif
     asm volatile(
         "{\n\t.reg .pred q;\n\t"
         "setp.ne.u32 q, %2, 0;\n\t"
@@ -211,6 +263,10 @@ struct Lane {
     static constexpr int kAddrWords = kWide ? 1 : kFullAddr ? PCM * DCM : (PCM * DCM + 1) / 2;
     uint32_t aw[kAddrWords];
     const uint16_t *cw;        // wide form: this lane's column of chk_word ([pc][DCM][G])
+#ifdef BPDC_CHECKS
+    const uint16_t *cw0;       // chk_word and its length (checked build)
+    long long n_cw;
+#endif
     uint32_t region_base;      // shared byte address of the group's region (wide form)
     uint32_t slot_base;        // shared byte address of slot 0
     uint32_t vm[kVmWords];     // bit (p*CVM + m): the variable at pass p has an m-th edge
@@ -229,6 +285,9 @@ struct Lane {
     __device__ __forceinline__ uint32_t addr(int p, int k) const
     {
         if constexpr (kWide) {
+#ifdef BPDC_CHECKS
+            if (!check_index(4, (long long)(cw - cw0) + (long long)(p * DCM + k) * G, n_cw)) return inf_addr;
+#endif
             return region_base + 4u * (uint32_t)__ldg(cw + (p * DCM + k) * G);
         } else {
             const int n = p * DCM + k;
@@ -243,6 +302,9 @@ struct Lane {
         for (int p = 0; p < PVM; ++p) {
             const int j = p * G + u;
             (void)j;
+#ifdef BPDC_CHECKS
+            if (p < g.pv && !check_index(5, (long long)p * G + u, g.n_pos)) { lamv[p] = f_inf(); continue; }
+#endif
             lamv[p] = p < g.pv ? __ldg(g.lam + (size_t)p * G + u) : f_inf();
         }
     }
@@ -255,6 +317,10 @@ struct Lane {
         this->slot_base = slot_base;
         cvalid = 0;
         cw = g.chk_word + u;
+#ifdef BPDC_CHECKS
+        cw0 = g.chk_word;
+        n_cw = g.n_chk_word;
+#endif
 #pragma unroll
         for (int w = 0; w < kAddrWords; ++w) aw[w] = 0;
 #pragma unroll
@@ -264,6 +330,9 @@ struct Lane {
 #pragma unroll
                 for (int k = 0; k < DCM; ++k) {
                     uint32_t v = kNoEdge;
+#ifdef BPDC_CHECKS
+                    if (p < g.pc && k < g.dc && !check_index(3, ((long long)p * g.dc + k) * G + u, g.n_chk_idx)) {} else
+#endif
                     if (p < g.pc && k < g.dc) v = __ldg(g.chk_idx + ((size_t)p * g.dc + k) * G + u);
                     const uint32_t a = ((v == kNoEdge) ? inf_word : slot_base + 4u * v) & 0xFFFFu;
                     const int n = p * DCM + k;
@@ -281,6 +350,9 @@ struct Lane {
             int deg = 0;
             (void)j;
             if (p < g.pv) {
+#ifdef BPDC_CHECKS
+                if (!check_index(5, (long long)p * G + u, g.n_pos)) continue;
+#endif
                 deg = __ldg(g.var_deg + (size_t)p * G + u);
                 if (deg == 0xFF) deg = 0; else vvalid |= 1u << p;
             }
@@ -327,6 +399,9 @@ struct Decoder {
 #pragma unroll
                     for (int m = 0; m < CVM; ++m) sts32(base + m * kSlot, (m < CMIN || ln.has(p, m)) ? v : 0u);
                 }
+#ifdef BPDC_CHECKS
+                if (post_row && ((ln.vvalid >> p) & 1u) && !post_ok(g, (long long)p * G + u)) {} else
+#endif
                 if (post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = lam;
             }
         }
@@ -489,6 +564,9 @@ struct Decoder {
                                 if (RC && !live) mag = f_inf();   // idle check: writes +inf back
                                 uint32_t out = __float_as_uint(mag) ^ Sm ^ (qb[k] & 0x80000000u);
                                 if (g.wts && live && a != ln.inf_addr) {   // weighted BP: r *= wc
+#ifdef BPDC_CHECKS
+                                    check_index(8, (long long)(min(t, g.w_T) - 1) * g.slots + ((a - ln.slot_base) >> 2), g.n_wts);
+#endif
                                     const float w = __ldg(g.wts + (size_t)(min(t, g.w_T) - 1) * g.slots +
                                                           ((a - ln.slot_base) >> 2));
                                     out = __float_as_uint(w * __uint_as_float(out));
@@ -540,6 +618,9 @@ struct Decoder {
                         if (CMIN > 0) sts32(base, lv);
                         else sts32_if(base, lv, ln.has(p, 0));
                     }
+#ifdef BPDC_CHECKS
+                    if (!FAST && post_row && ((ln.vvalid >> p) & 1u) && !post_ok(g, (long long)p * G + u)) {} else
+#endif
                     if (!FAST && post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = Lp;
                 }
             }
@@ -654,6 +735,9 @@ struct Decoder {
                 if (post_row) {
 #pragma unroll
                     for (int p = 0; p < PVM; ++p)
+#ifdef BPDC_CHECKS
+                        if (p < g.pv && ((ln.vvalid >> p) & 1u) && !post_ok(g, (long long)p * G + u)) {} else
+#endif
                         if (p < g.pv && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = ln.lamv[p];
                 }
             } else {
@@ -675,6 +759,9 @@ struct Decoder {
                         g, gshot, u, G,
                         [&](int, uint32_t e) {
                             const uint32_t s0 = e & 0xFFFFu;
+#ifdef BPDC_CHECKS
+                            if (s0 == kNoEdge ? !check_index(5, e >> 16, g.n_pos) : !check_index(1, s0, g.slots)) return f_inf();
+#endif
                             return s0 == kNoEdge ? __ldg(g.lam + (e >> 16)) : slot[s0];
                         },
                         [&](int, uint32_t e) { atomicOr(cm + ((e >> 16) >> 5), 1u << ((e >> 16) & 31)); });
@@ -717,6 +804,9 @@ struct Decoder {
                     if ((hd >> p) & 1u) {
                         const int j = p * G + u;
                         const int c = __ldg(g.pos_col + j);
+#ifdef BPDC_CHECKS
+                        if (!check_index(7, c, g.N)) continue;
+#endif
                         atomicOr(cm + (c >> 5), 1u << (c & 31));
                         const uint32_t *lc = g.l_bits + (size_t)j * g.KW;
                         for (int x = 0; x < g.KW; ++x) {
@@ -867,6 +957,21 @@ static const Variant kVariants[] = {
 
 int num_variants() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
 const Variant &variant(int id) { return kVariants[id]; }
+
+#ifdef BPDC_CHECKS
+bool check_status(int *site, long long *index)
+{
+    unsigned long long v[2] = {0ull, 0ull};
+    if (cudaMemcpyFromSymbol(v, g_check, sizeof(v)) != cudaSuccess) return false;
+    const unsigned long long z[2] = {0ull, 0ull};
+    if (cudaMemcpyToSymbol(g_check, z, sizeof(z)) != cudaSuccess) return false;
+    *site = (int)v[0];
+    *index = (long long)v[1];
+    return true;
+}
+#else
+bool check_status(int *, long long *) { return false; }
+#endif
 
 static const void *variant_fn(int id)
 {

@@ -24,6 +24,17 @@ def test_every_declared_symbol_is_exported(lib):
     assert pkg.version().startswith("bpdc")
 
 
+def test_checked_build_exports_every_declared_symbol(lib):
+    """libbpdc_checked.so (the bounds-checked debugging build) exports the same
+    C-ABI; only it implements bpdc_check_status."""
+    chk = ctypes.CDLL(build.LIB_CHECKED)
+    for s in pkg.declared_symbols():
+        assert hasattr(chk, s), s
+    site, index = ctypes.c_int32(), ctypes.c_int64()
+    assert lib.bpdc_check_status(0, ctypes.byref(site), ctypes.byref(index)) == _bpdc.ERR_UNSUPPORTED
+    assert chk.bpdc_check_status(0, None, None) == _bpdc.ERR_INVALID_ARG
+
+
 def test_default_options(lib):
     o = _bpdc._Opts()
     lib.bpdc_opts_default(ctypes.byref(o))
