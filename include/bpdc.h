@@ -266,6 +266,15 @@ int bpdc_sample(bpdc_graph_t g, int64_t B, uint64_t seed, uint64_t shot_offset,
  * clears it. */
 int bpdc_graph_sync_status(bpdc_graph_t g, void *stream);
 
+/* Failure injection for tests (the paper has none).  After `skip` more
+ * allocations, the next `count` device or page-locked allocations that the
+ * library makes itself (graph arenas, launch rings and their page-locked
+ * descriptor mirrors, host-decode staging) fail as if memory were exhausted,
+ * without calling the allocator, so the call making them returns BPDC_ERR_OOM
+ * and keeps its graph as it was.  count = 0 turns the injection off.  Process-
+ * wide; BPDC_ERR_INVALID_ARG if skip or count is negative. */
+int bpdc_debug_fail_allocations(int32_t skip, int32_t count);
+
 /* Bounds checks (a debugging aid; the paper has none).  The library is also
  * built as libbpdc_checked.so with -DBPDC_CHECKS: there the decode kernel
  * compares every shared-memory message access with the block's dynamic shared

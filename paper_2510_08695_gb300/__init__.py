@@ -2,6 +2,6 @@
 with degeneracy cutting, as hand-written sm_103a CUDA behind the C-ABI of
 ``libbpdc.so`` (declared in ``include/bpdc.h``)."""
 from ._bpdc import (  # noqa: F401
-    BpdcError, Graph, Options, check_status, decode_host, decode_multi, decode_multi_noalloc, declared_symbols, library_path, load,
+    BpdcError, Graph, Options, check_status, debug_fail_allocations, decode_host, decode_multi, decode_multi_noalloc, declared_symbols, library_path, load,
     measure_smem_peak, version,
 )

@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True):
         "bpdc_sample": (ctypes.c_int, [vp, i64, u64, u64, vp, vp, vp, vp]),
         "bpdc_graph_sync_status": (ctypes.c_int, [vp, vp]),
         "bpdc_check_status": (ctypes.c_int, [i32, _i32p, ctypes.POINTER(ctypes.c_int64)]),
+        "bpdc_debug_fail_allocations": (ctypes.c_int, [i32, i32]),
         "bpdc_graph_set_weights": (ctypes.c_int, [vp, vp, i32, ctypes.c_float]),
         "bpdc_wbp_workspace_size": (ctypes.c_int, [vp, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]),
         "bpdc_wbp_forward": (ctypes.c_int, [vp, i64, vp, vp, i32, ctypes.c_float, i32, vp, vp, ctypes.c_size_t,
@@ -333,6 +334,12 @@ def _batches(items):
         arr[i].shot_offset = int(it.get("shot_offset", 0))
         arr[i].out = g._outputs(it["out"], it.get("obs_true"), it.get("counters"), it.get("cut_in"))
     return arr
+
+
+def debug_fail_allocations(skip: int, count: int):
+    """bpdc_debug_fail_allocations: after ``skip`` allocations of the library,
+    the next ``count`` fail as if memory were exhausted (0: off)."""
+    _check(load().bpdc_debug_fail_allocations(int(skip), int(count)))
 
 
 def check_status(device: int = 0):

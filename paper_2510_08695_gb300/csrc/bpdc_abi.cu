@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <limits>
 #include <cstdarg>
@@ -35,6 +36,36 @@ int fail(int code, const char *fmt, ...)
 int cuda_fail(cudaError_t e, const char *what)
 {
     return fail(BPDC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Failure injection for tests (bpdc_debug_fail_allocations): after
+// g_alloc_skip more allocations, the next g_alloc_fail device or page-locked
+// allocations of the library fail as if memory were exhausted.
+std::mutex g_alloc_mu;
+int g_alloc_skip = 0, g_alloc_fail = 0;
+
+bool injected_alloc_failure()
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_alloc_fail <= 0) return false;
+    if (g_alloc_skip > 0) {
+        --g_alloc_skip;
+        return false;
+    }
+    --g_alloc_fail;
+    return true;
+}
+
+cudaError_t lib_malloc(void **p, size_t n)
+{
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, n);
+}
+
+cudaError_t lib_malloc_host(void **p, size_t n)
+{
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+    return cudaMallocHost(p, n);
 }
 
 // Makes `dev` current for the scope and restores the caller's device.
@@ -348,7 +379,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     const size_t o_wts = put(blob, P.wts);
     const size_t o_err = put(blob, std::vector<int32_t>(4, 0));
     void *arena = nullptr;
-    e = cudaMalloc(&arena, blob.size());
+    e = lib_malloc(&arena, blob.size());
     if (e != cudaSuccess) return fail(BPDC_ERR_OOM, "cudaMalloc of %zu bytes: %s", blob.size(), cudaGetErrorString(e));
     e = cudaMemcpy(arena, blob.data(), blob.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(arena); return cuda_fail(e, "upload of the graph"); }
@@ -407,9 +438,9 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
 int ring_init(bpdc_graph_s *g)
 {
     const size_t per = sizeof(BatchDesc) * kMaxBatches + 256;
-    cudaError_t e = cudaMalloc(&g->ring_mem, per * kRing);
+    cudaError_t e = lib_malloc(&g->ring_mem, per * kRing);
     if (e != cudaSuccess) return fail(BPDC_ERR_OOM, "ring allocation: %s", cudaGetErrorString(e));
-    e = cudaMallocHost(&g->ring_host, sizeof(BatchDesc) * kMaxBatches * kRing);
+    e = lib_malloc_host(&g->ring_host, sizeof(BatchDesc) * kMaxBatches * kRing);
     if (e != cudaSuccess) return fail(BPDC_ERR_OOM, "pinned ring allocation: %s", cudaGetErrorString(e));
     for (int s = 0; s < kRing; ++s) {
         char *b = (char *)g->ring_mem + per * s;
@@ -844,7 +875,7 @@ int bpdc_decode_host(const bpdc_batch *batches, int32_t n, int64_t chunk_shots, 
         if (owner->stage) cudaFree(owner->stage);
         owner->stage = nullptr;
         owner->stage_set_bytes = 0;
-        e = cudaMalloc(&owner->stage, 2 * set_bytes);
+        e = lib_malloc(&owner->stage, 2 * set_bytes);
         if (e != cudaSuccess)
             return fail(BPDC_ERR_OOM, "host-decode staging of %zu bytes: %s", 2 * set_bytes, cudaGetErrorString(e));
         owner->stage_set_bytes = set_bytes;
@@ -1013,6 +1044,15 @@ int bpdc_graph_sync_status(bpdc_graph_t g, void *stream)
         cudaMemcpy(g->dg.err_flag, &zero, sizeof(zero), cudaMemcpyHostToDevice);
         return fail(flag, "device reported error %d", flag);
     }
+    return BPDC_OK;
+}
+
+int bpdc_debug_fail_allocations(int32_t skip, int32_t count)
+{
+    if (skip < 0 || count < 0) return fail(BPDC_ERR_INVALID_ARG, "skip and count must be >= 0");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc_skip = count > 0 ? skip : 0;
+    g_alloc_fail = count;
     return BPDC_OK;
 }
 

@@ -128,6 +128,13 @@ def test_host_decode_rejects_bad_arguments(lib):
     assert lib.bpdc_decode_host(arr, 1, 0, None) == _bpdc.ERR_INVALID_ARG   # no graph
 
 
+def test_allocation_failure_hook_arguments(lib):
+    assert lib.bpdc_debug_fail_allocations(-1, 1) == _bpdc.ERR_INVALID_ARG
+    assert lib.bpdc_debug_fail_allocations(0, -1) == _bpdc.ERR_INVALID_ARG
+    assert lib.bpdc_debug_fail_allocations(2, 1) == 0
+    assert lib.bpdc_debug_fail_allocations(0, 0) == 0
+
+
 def test_valid_problem_needs_a_device_or_succeeds(lib):
     H, L, D, p = _small()
     rc, out = _create(lib, H, L, D, p)
