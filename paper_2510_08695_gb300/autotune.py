@@ -12,6 +12,15 @@ Results are identical for every variant; only the speed differs.
 from __future__ import annotations
 
 
+def choose(times: dict, incumbent: int, margin: float = 0.02) -> int:
+    """The variant to keep given measured times: the fastest, unless the
+    incumbent was timed and the fastest beats it by no more than ``margin``."""
+    best = min(times, key=times.get)
+    if incumbent in times and times[best] > (1.0 - margin) * times[incumbent]:
+        return incumbent
+    return best
+
+
 def autotune(graph, syndromes, shot_offset: int = 0, reps: int = 2, persistent: bool = True,
              verbose: bool = False, margin: float = 0.02) -> dict:
     """Selects the fastest kernel variant for ``graph`` on ``syndromes``.
@@ -38,8 +47,6 @@ def autotune(graph, syndromes, shot_offset: int = 0, reps: int = 2, persistent: 
         if verbose:
             print(f"kernel {k}: G={graph.info['threads_per_shot']} blocks/SM={graph.info['blocks_per_sm']} "
                   f"{times[k]:.3f} ms", flush=True)
-    best = min(times, key=times.get)
-    if incumbent in times and times[best] > (1.0 - margin) * times[incumbent]:
-        best = incumbent
+    best = choose(times, incumbent, margin)
     graph.set_kernel(best)
     return {"best": best, "ms": times}
