@@ -96,8 +96,18 @@ void bpdc_opts_default(bpdc_opts *o);
  * required; empty columns are allowed).  L: K x N (K may be 0, rows may be
  * empty).  D: Md x N (Md may be 0; empty rows are skipped by the cut).
  * priors: N host doubles in (0, 1/2].  The library copies everything; the
- * caller may free its arrays on return.  Limits: N, M <= 65535, row weight of
- * H <= 16, column weight of H <= 8, row weight of D <= 64.
+ * caller may free its arrays on return.  Limits: row weight of D <= 64, and H
+ * must fit one compiled kernel variant (bpdc_graph_set_kernel), of which
+ * these are the widest:
+ *     check rule   M <=   N <=   row weight   column weight
+ *     min-sum        96    160   6 exactly    3 exactly     (BB-like, 32 threads)
+ *     min-sum       128    256   <= 8         1..4          (32 threads)
+ *     min-sum      1536   2560   7 exactly    3..4          (HGP-like)
+ *     min-sum      1024   3072   <= 8         2..3          (phenomenological)
+ *     min-sum      1024   9216   <= 35        2..6          (circuit-level)
+ *     product-sum   128    128   <= 4         1..2          (surface codes)
+ *     product-sum    96    160   6 exactly    3 exactly     (BB-like)
+ * Larger graphs are UNSUPPORTED.
  * Errors: INVALID_ARG (null pointer, malformed CSR, prior outside (0, 1/2],
  * option out of range), DIM_MISMATCH (column counts differ),
  * UNSUPPORTED (a limit above is exceeded), OOM, CUDA. */
@@ -181,7 +191,8 @@ typedef struct {
  * not depend on how shots are split across calls or GPUs.  persistent = 1
  * launches one resident grid that pulls shots from a device work counter;
  * persistent = 0 launches the plain per-batch grid (one group per shot).
- * Both give identical results.  Asynchronous on `stream`. */
+ * Both give identical results.  At most 4 278 190 080 (2^32 - 2^24) shots per
+ * call (UNSUPPORTED above).  Asynchronous on `stream`. */
 int bpdc_decode(bpdc_graph_t g, int64_t B, const uint32_t *syndromes, uint64_t shot_offset,
                 const bpdc_outputs *out, int persistent, void *stream);
 
@@ -198,7 +209,9 @@ typedef struct {
  * launches as the compiled kernel variants allow (one per variant), with the
  * shots of all batches of a variant behind one device work counter.  All
  * graphs must live on the same device; results equal those of bpdc_decode
- * on each batch.  Asynchronous on `stream`. */
+ * on each batch.  A launch takes at most 2^32 - 2^24 shots: longer lists are
+ * split over several launches, and a single batch above that size is
+ * UNSUPPORTED.  Asynchronous on `stream`. */
 int bpdc_decode_multi(const bpdc_batch *batches, int32_t n_batches, void *stream);
 
 /* Decoding from host memory (the paper has no counterpart: this is the end-to-
@@ -227,13 +240,14 @@ int bpdc_decode_host(const bpdc_batch *batches, int32_t n_batches, int64_t chunk
  * allocator, code embedded in a host framework whose allocator owns all device
  * memory, or a stream that is being captured into a CUDA graph.  This call
  * allocates nothing: the persistent kernel's scratch (its device work counter
- * and the descriptors of up to 16 batches, about 5 KB) lives in a fixed device
+ * and the descriptors of up to 16 batches: 256 + 16 x 344 = 5760 bytes) lives in a fixed device
  * array of the library, which every GPU that loads the library holds until the
  * process exits.  The caller still passes every input and output, and the
  * graphs must already exist.
  *   - At most 16 batches per call, all on graphs that use the same kernel
- *     variant (bpdc_graph_info.kernel_id); otherwise BPDC_ERR_UNSUPPORTED with
- *     a message, and nothing is launched.
+ *     variant (bpdc_graph_info.kernel_id), and at most 2^32 - 2^24 shots in
+ *     all; otherwise BPDC_ERR_UNSUPPORTED with a message, and nothing is
+ *     launched.
  *   - The first call on a device looks up the array's device address; make
  *     that first call before any stream capture on that device.
  *   - Every call reuses the same array (the work counter is cleared at the

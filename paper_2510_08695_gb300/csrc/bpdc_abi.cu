@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <cmath>
 #include <limits>
 #include <cstdarg>
@@ -168,9 +169,11 @@ namespace {
 // Message-slot layout of the packing: variable j at lane j % G, pass j / G,
 // its m-th edge (ascending check index) in slot ((j/G)*cv + m)*G + j%G.
 struct Packed {
-    int G, pc, pv, dc, cv, slots, cmw, region, KW, NW, MW;
+    int G, pc, pv, dc, cv, slots, cmw, region, KW, NW, MW, tab_off;
+    std::vector<int> pass_off;   // [pv + 1] slots (per lane) before each pass
     std::vector<uint16_t> chk_idx;
     std::vector<uint16_t> chk_word;
+    std::vector<uint16_t> chk_tab;   // [ceil(row width / 8)][G][8] (wide variants with a table)
     std::vector<uint8_t> var_deg;
     std::vector<float> lam;
     std::vector<int32_t> d_ptr;
@@ -210,7 +213,22 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     if (cmin < v.cv_min) return false;
     P.dc = std::max(dmax, 1);
     P.cv = v.cv_max;
-    const long slots = (long)P.pv * P.cv * G;
+    // slots per pass (the variant's profile), and the degrees it can hold
+    std::vector<int> pass_cv(P.pv);
+    P.pass_off.assign(P.pv + 1, 0);
+    for (int p = 0; p < P.pv; ++p) {
+        pass_cv[p] = prof_cv(v.prof, v.cv_max, p);
+        P.pass_off[p + 1] = P.pass_off[p] + pass_cv[p];
+    }
+    if (v.prof) {
+        // with degrees sorted into the passes, the i-th largest degree must fit
+        // the pass of position i
+        std::vector<int> ds(deg);
+        std::sort(ds.begin(), ds.end(), std::greater<int>());
+        for (int j = 0; j < N; ++j)
+            if (ds[j] > pass_cv[j / G]) return false;
+    }
+    const long slots = (long)P.pass_off[P.pv] * G;
     if (slots > 65535) return false;
     P.slots = (int)slots;
     P.cmw = (P.pv * G + 31) / 32;
@@ -219,19 +237,30 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     P.KW = (K + 31) / 32;
     int region = 12 + P.slots + P.cmw + std::max(P.KW, 1);   // 12 misc words (see the kernels)
     region = (region + 3) & ~3;
+    // the wide form with an edge table keeps each lane's check-edge word
+    // indices in shared memory after the group's other words (16-byte entries)
+    const int tab_chunks = (std::max(v.dc_max, P.dc) + kTabEdges - 1) / kTabEdges;
+    P.tab_off = 0;
+    if (v.tab) {   // one check pass per lane (the table holds one row per lane)
+        if (v.pc_max != 1) return false;
+        P.tab_off = region;
+        region += tab_chunks * G * 4;
+    }
     P.region = region;
     // check edges are kept as 16-bit values in the kernels: byte addresses
     // below 64 KB (the block's dynamic shared memory plus the reserved 1 KB),
     // or, in the wide form, word indices of the group's region
-    if (wide_slots(G, v.pv_max, v.cv_max)) {
-        if (region > 65535 || (long)(v.block_threads / G) * region * 4 > kMaxSmemPerBlock) return false;
-    } else if ((long)(v.block_threads / G) * region * 4 + 1024 > 65535) {
+    if (wide_slots(G, prof_off(v.prof, v.cv_max, v.pv_max))) {
+        if (12 + P.slots + P.cmw > 65535 || (long)(v.block_threads / G) * region * 4 > kMaxSmemPerBlock) return false;
+    } else if (v.tab || (long)(v.block_threads / G) * region * 4 + 1024 > 65535) {
         return false;
     }
     // variable placement and edge order (bpdc_layout.cu)
     const int npos = P.pv * G;
     Layout lay;
-    plan_layout(M, N, g.H.ptr, g.H.col, G, npos, P.dc, g.layout != 0, lay);
+    plan_layout(M, N, g.H.ptr, g.H.col, G, npos, P.dc, g.layout != 0, pass_cv, lay);
+    for (int j = 0; j < N; ++j)
+        if (deg[j] > pass_cv[lay.pos_of_var[j] / G]) return false;
     // edge -> slot of its variable
     std::vector<int> fill(N, 0);
     std::vector<int> edge_slot(g.H.col.size());
@@ -240,7 +269,7 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
             const int j = g.H.col[a];
             const int pos = lay.pos_of_var[j];
             const int m = fill[j]++;
-            edge_slot[a] = ((pos / G) * P.cv + m) * G + (pos % G);
+            edge_slot[a] = (P.pass_off[pos / G] + m) * G + (pos % G);
         }
     if (!g.w_host.empty()) {   // learned weights into message-slot order
         const size_t E = g.H.col.size();
@@ -266,6 +295,15 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
                     const uint16_t e = P.chk_idx[((size_t)p * P.dc + k) * G + u];
                     if (e != kNoEdge) P.chk_word[((size_t)p * dcw + k) * G + u] = (uint16_t)(12 + e);
                 }
+        if (v.tab) {
+            // 8 edges of one lane per 16-byte entry: entry (c, u) holds edges
+            // 8c .. 8c+7 of lane u (one check pass), padded with the +inf word
+            P.chk_tab.assign((size_t)tab_chunks * G * kTabEdges, (uint16_t)2);
+            for (int k = 0; k < std::min(dcw, tab_chunks * kTabEdges); ++k)
+                for (int u = 0; u < G; ++u)
+                    P.chk_tab[((size_t)(k / kTabEdges) * G + u) * kTabEdges + k % kTabEdges] =
+                        P.chk_word[(size_t)k * G + u];
+        }
     }
     P.var_deg.assign((size_t)npos, 0xFF);   // 0xFF: no variable at this position
     P.lam.assign((size_t)npos, std::numeric_limits<float>::infinity());
@@ -295,7 +333,7 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
             const int pos = lay.pos_of_var[j];
             // slot of the variable's first edge (it holds L after the last
             // iteration); kNoEdge for a variable without edges (L = lambda)
-            const uint32_t s0 = deg[j] > 0 ? (uint32_t)(((pos / G) * P.cv) * G + (pos % G)) : kNoEdge;
+            const uint32_t s0 = deg[j] > 0 ? (uint32_t)(P.pass_off[pos / G] * G + (pos % G)) : kNoEdge;
             P.d_ent.push_back(s0 | ((uint32_t)pos << 16));
             P.d_col.push_back(j);
         }
@@ -330,7 +368,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     // automatic preference: one warp per shot for small graphs (3 blocks per
     // SM before 4: the same speed with fewer spills), then the 256- and
     // 512-thread groups
-    static const int kOrder[] = {7, 0, 12, 5, 11, 1, 3, 2, 4, 6, 13};
+    static const int kOrder[] = {7, 0, 12, 5, 11, 1, 15, 3, 2, 4, 6, 14, 13};
     Packed P{};
     int vid = -1;
     for (int id : kOrder) {
@@ -359,7 +397,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     // device arena
     std::vector<char> blob;
     const size_t o_chk = put(blob, P.chk_idx), o_deg = put(blob, P.var_deg), o_lam = put(blob, P.lam);
-    const size_t o_chkw = put(blob, P.chk_word);
+    const size_t o_chkw = put(blob, P.chk_word), o_tab = put(blob, P.chk_tab);
     const size_t o_dptr = put(blob, P.d_ptr), o_dent = put(blob, P.d_ent), o_l = put(blob, P.l_pos);
     const size_t o_dcol = put(blob, P.d_col), o_lcol = put(blob, P.l_cols), o_pcol = put(blob, P.pos_col);
     const size_t o_hptr = put(blob, g->H.ptr), o_hcol = put(blob, g->H.col), o_thr = put(blob, P.thr);
@@ -402,6 +440,8 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     d.kernel_id = vid;
     d.chk_idx = (const uint16_t *)(base + o_chk);
     d.chk_word = (const uint16_t *)(base + o_chkw);
+    d.chk_tab = (const uint4 *)(base + o_tab);
+    d.tab_off = P.tab_off;
     d.var_deg = (const uint8_t *)(base + o_deg);
     d.lam = (const float *)(base + o_lam);
     d.d_ptr = (const int32_t *)(base + o_dptr);
@@ -504,6 +544,9 @@ void fill_desc(BatchDesc &d, const bpdc_graph_s *g, int64_t B, const uint32_t *s
 int enqueue(bpdc_graph_s *g, int s, int n, int64_t total, int vid, int smem, bool persistent,
             cudaStream_t stream)
 {
+    if (total > kMaxLaunchShots)
+        return fail(BPDC_ERR_UNSUPPORTED, "at most %lld shots per launch (got %lld)", (long long)kMaxLaunchShots,
+                    (long long)total);
     RingSlot &rs = g->ring[s];
     cudaError_t e = cudaMemcpyAsync(rs.dev_desc, rs.host_desc, sizeof(BatchDesc) * n,
                                     cudaMemcpyHostToDevice, stream);
@@ -696,7 +739,7 @@ int bpdc_layout_plan(const bpdc_csr *H, int32_t G, int32_t optimize, int32_t *po
     for (int i = 0; i < h.rows; ++i) dc = std::max(dc, h.ptr[i + 1] - h.ptr[i]);
     const int npos = std::max(1, (h.cols + G - 1) / G) * G;
     Layout lay;
-    plan_layout(h.rows, h.cols, h.ptr, h.col, G, npos, dc, optimize != 0, lay);
+    plan_layout(h.rows, h.cols, h.ptr, h.col, G, npos, dc, optimize != 0, std::vector<int>(), lay);
     std::copy(lay.pos_of_var.begin(), lay.pos_of_var.end(), pos_of_var);
     // edge_round is reported in the caller's CSR order (copy_csr sorted each row)
     for (int i = 0; i < h.rows; ++i)
@@ -805,6 +848,8 @@ int bpdc_decode_multi(const bpdc_batch *batches, int32_t n, void *stream)
         int64_t total = 0;
         while (i < order.size() && cnt < kMaxBatches && batches[order[i]].graph->variant == vid) {
             const bpdc_batch &bt = batches[order[i]];
+            // a launch takes at most kMaxLaunchShots: the next one takes the rest
+            if (cnt > 0 && total + bt.B > kMaxLaunchShots) break;
             if (bt.B > 0) {
                 fill_desc(owner->ring[s].host_desc[cnt], bt.graph, bt.B, bt.syndromes, bt.shot_offset, &bt.out, total);
                 total += bt.B;
@@ -999,6 +1044,9 @@ int bpdc_decode_multi_noalloc(const bpdc_batch *batches, int32_t n, void *stream
         ++cnt;
     }
     if (cnt == 0) return BPDC_OK;
+    if (total > kMaxLaunchShots)
+        return fail(BPDC_ERR_UNSUPPORTED, "at most %lld shots per call (got %lld)", (long long)kMaxLaunchShots,
+                    (long long)total);
     const Variant &v = variant(vid);
     const int64_t need = (total + v.block_threads / v.G - 1) / (v.block_threads / v.G);
     const int64_t grid = std::min<int64_t>((int64_t)owner->sm_count * bps, need);

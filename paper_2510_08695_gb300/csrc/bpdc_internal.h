@@ -15,11 +15,28 @@ constexpr uint16_t kNoEdge = 0xFFFF;
 // Limits of the compiled kernel variants.
 constexpr int kMaxDRowWeight = 64;
 
-// Check edges are kept as 16-bit values in registers.  A group whose message
-// slots fit in 64 KB of shared memory keeps byte addresses in the block's
-// shared window; a larger group (one per block) keeps word indices into its
-// own region and scales them when it loads or stores.
-constexpr bool wide_slots(int G, int pv, int cv) { return (long)G * pv * cv * 4 > 60 * 1024; }
+// Message slots per variable pass.  A variant's profile holds 4 bits per pass
+// (pass p in bits 4p .. 4p+3, a non-increasing sequence): pass p gives each of
+// its variables prof_cv slots, so that a graph whose variables are sorted by
+// degree into the passes stores no padding for the long tail of low-degree
+// columns.  Profile 0: every pass has cv slots.
+constexpr int prof_cv(uint64_t prof, int cv, int p) { return prof ? (int)((prof >> (4 * p)) & 0xFu) : cv; }
+// Slots of the passes before p (per lane).
+constexpr int prof_off(uint64_t prof, int cv, int p)
+{
+    int s = 0;
+    for (int i = 0; i < p; ++i) s += prof_cv(prof, cv, i);
+    return s;
+}
+
+// Check edges are kept as 16-bit values.  A group whose message slots fit in
+// 64 KB of shared memory keeps byte addresses in the block's shared window; a
+// larger group (one per block) keeps word indices into its own region and
+// scales them when it loads or stores.  slots_per_lane: the variant's slots of
+// all passes of one lane.
+constexpr bool wide_slots(int G, int slots_per_lane) { return (long)G * slots_per_lane * 4 > 60 * 1024; }
+// Check-edge word indices per 16-byte entry of the shared-memory edge table.
+constexpr int kTabEdges = 8;
 
 // Device-resident decoding problem, laid out for a group of G threads per
 // shot.  Variable j sits at lane j % G, pass j / G; check i at lane i % G,
@@ -53,6 +70,10 @@ struct DevGraph {
     const uint16_t *chk_word;    // [pc][variant row width][G] the same as word indices of the group's
                                  // region (the +inf word, 2, for none and for padding): read per
                                  // access by the wide kernels
+    const uint4 *chk_tab;        // [ceil(row width / 8)][G] the same word indices, 8 per entry (edge
+                                 // 8c + e of lane u in 16-bit half e of entry (c, u)): copied into
+                                 // shared memory by the wide kernels with an edge table
+    int32_t tab_off;             // word offset of that shared copy inside the group's region
     const uint8_t *var_deg;      // [pv][G] degree of the variable (0 past N)
     const float *lam;            // [pv][G] prior LLR ln((1-p)/p)
     const int32_t *d_ptr;        // [Md+1] rows of D
@@ -108,6 +129,8 @@ struct Variant {
     int rule;            // check rule: 0 normalized min-sum, 1 product-sum
     int block_threads;
     int min_blocks;      // launch bound: resident blocks per SM the register budget allows
+    uint64_t prof;       // slots per variable pass (prof_cv); 0: cv_max in every pass
+    bool tab;            // check-edge table in shared memory (wide form only)
 };
 
 // Placement of variables on positions and order of the edges inside each
@@ -118,8 +141,11 @@ struct Layout {
     std::vector<int32_t> var_at_pos;   // [npos], -1 where empty
     std::vector<int32_t> edge_round;   // [nnz(H)] round k of each edge within its check
 };
+// pass_cv (empty: no limit): slots of each variable pass; a variable of degree
+// d then sits in a pass with at least d slots (passes fill in order of
+// decreasing degree, so pass_cv must not increase).
 void plan_layout(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col, int G,
-                 int npos, int dc, bool optimize, Layout &out);
+                 int npos, int dc, bool optimize, const std::vector<int> &pass_cv, Layout &out);
 
 int num_variants();
 // Checked builds: the first failed bounds check since the last call (site 0:
@@ -129,6 +155,12 @@ const Variant &variant(int id);
 // Occupancy query and launch of variant `id`.
 cudaError_t variant_attributes(int id, int smem_bytes, int *blocks_per_sm, int *regs);
 cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_bytes, cudaStream_t s);
+
+// Most shots one decode launch takes: groups of more than 32 threads pass
+// their work ticket to each other through a 32-bit shared word, and every
+// group draws one ticket past the last shot, so every ticket of a launch stays
+// below 2^32 with room for 2^24 groups.
+constexpr int64_t kMaxLaunchShots = (int64_t(1) << 32) - (int64_t(1) << 24);
 
 // Largest number of batches one allocation-free launch takes (its scratch is a
 // fixed device array).

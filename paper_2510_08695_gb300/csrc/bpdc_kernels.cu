@@ -38,6 +38,7 @@
 // maximum, breaks ties with the SplitMix64 hash of (shot, row) and sets the
 // winner's bit in a shared cut mask; BP runs again with cut variables pinned
 // to +inf and the priors of Sec. III.B.
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -188,6 +189,17 @@ __device__ __forceinline__ float phi(float x) { return log1pf(2.0f / expm1f(x));
 // phi(sum_j phi(x_j)) = -log sum_j e^-x_j + O(e^-2m), which lowers by exactly s.
 constexpr float kPhiShift = 20.0f;
 
+// A check's minimum |q| as it enters the outgoing message: at most the cap,
+// and 0 below the smallest normal float.  The hard-decision tag turns a
+// message that is exactly 0 into the smallest denormal when its sender's
+// decision is 1; without the flush that denormal would move an exact 0 of the
+// rule (and with it a posterior L = 0, whose decision is 1) off zero.  No
+// message of the rule is nonzero and that small otherwise.
+__device__ __forceinline__ float clamp_min(float m)
+{
+    return m < 1.17549435e-38f ? 0.0f : fminf(m, kLlrCap);
+}
+
 // Shared words at the start of every group's region: 0-1 shot broadcast
 // (double buffered), 2 the +inf word, 4-11 the per-batch counters.
 constexpr int kMiscWords = 12;
@@ -222,6 +234,17 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
     return r;
 }
 
+// 16-byte load of a table entry (four words).
+__device__ __forceinline__ uint4 lds128(uint32_t a)
+{
+#ifdef BPDC_CHECKS
+    if (!smem_ok(a, 1) || !smem_ok(a + 12u, 1)) return make_uint4(0x20002u, 0x20002u, 0x20002u, 0x20002u);
+#endif
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
 __device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
 {
 #ifdef BPDC_CHECKS
@@ -247,11 +270,20 @@ __device__ __forceinline__ void sts32_if(uint32_t a, uint32_t v, bool pred)
 // switches to a batch of another graph).  CMIN: every variable has at least
 // CMIN edges (slots below CMIN need no store predicate); RC: every check has
 // exactly DCM edges.
-template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC>
+template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, uint64_t PROF, bool TAB>
 struct Lane {
-    static constexpr int kVmWords = (PVM * CVM + 31) / 32;
+    // slots of pass p (per lane) and the slots before it
+    static constexpr int cv(int p) { return prof_cv(PROF, CVM, p); }
+    static constexpr int off(int p) { return prof_off(PROF, CVM, p); }
+    static constexpr int kSlotsPerLane = prof_off(PROF, CVM, PVM);
+    static constexpr int kVmWords = (kSlotsPerLane + 31) / 32;
 
-    static constexpr bool kWide = wide_slots(G, PVM, CVM);
+    static constexpr bool kWide = wide_slots(G, kSlotsPerLane);
+    // wide form with the check-edge word indices in shared memory: 16-byte
+    // entries of 8 indices, entry c of this lane at tab + 16 * c * G
+    static constexpr bool kTab = kWide && TAB;
+    static constexpr int kTabChunks = (DCM + kTabEdges - 1) / kTabEdges;
+    static_assert(!kTab || (PCM == 1 && kTabChunks > 0), "the shared edge table holds one check pass");
     // shared byte address of each check edge's slot (the +inf word if none):
     // one register per edge when a lane has at most 40 check edges (no
     // unpacking at each access), else two 16-bit values per register.  The
@@ -263,6 +295,7 @@ struct Lane {
     static constexpr int kAddrWords = kWide ? 1 : kFullAddr ? PCM * DCM : (PCM * DCM + 1) / 2;
     uint32_t aw[kAddrWords];
     const uint16_t *cw;        // wide form: this lane's column of chk_word ([pc][DCM][G])
+    uint32_t tab;              // wide form with a table: shared byte address of this lane's entry 0
 #ifdef BPDC_CHECKS
     const uint16_t *cw0;       // chk_word and its length (checked build)
     long long n_cw;
@@ -278,9 +311,12 @@ struct Lane {
 
     __device__ __forceinline__ bool has(int p, int m) const
     {
-        const int n = p * CVM + m;
+        const int n = off(p) + m;
         return (vm[n >> 5] >> (n & 31)) & 1u;
     }
+
+    // Shared byte address of the word with index w of the group's region.
+    __device__ __forceinline__ uint32_t word_addr(uint32_t w) const { return region_base + 4u * w; }
 
     __device__ __forceinline__ uint32_t addr(int p, int k) const
     {
@@ -317,6 +353,20 @@ struct Lane {
         this->slot_base = slot_base;
         cvalid = 0;
         cw = g.chk_word + u;
+        tab = region_base + 4u * (uint32_t)g.tab_off + 16u * (uint32_t)u;
+        if constexpr (kTab) {
+            // this lane's entries of the edge table into shared memory; only
+            // this lane reads them back, so no barrier is needed
+#pragma unroll
+            for (int c = 0; c < kTabChunks; ++c) {
+                const uint4 e = __ldg(g.chk_tab + (size_t)c * G + u);
+#ifdef BPDC_CHECKS
+                if (!smem_ok(tab + 16u * c * G, 2) || !smem_ok(tab + 16u * c * G + 12u, 2)) continue;
+#endif
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tab + 16u * c * G), "r"(e.x),
+                             "r"(e.y), "r"(e.z), "r"(e.w));
+            }
+        }
 #ifdef BPDC_CHECKS
         cw0 = g.chk_word;
         n_cw = g.n_chk_word;
@@ -358,19 +408,24 @@ struct Lane {
             }
 #pragma unroll
             for (int m = 0; m < CVM; ++m) {
-                const int n = p * CVM + m;
-                if (m < deg) vm[n >> 5] |= 1u << (n & 31);
+                const int n = off(p) + m;
+                if (m < cv(p) && m < deg) vm[n >> 5] |= 1u << (n & 31);
             }
         }
         reload_lam(g, u);
     }
 };
 
-template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int RULE>
+template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int RULE, uint64_t PROF, bool TAB>
 struct Decoder {
-    using L = Lane<G, PCM, DCM, PVM, CVM, CMIN, RC>;
-    static constexpr uint32_t kPass = 4u * CVM * G;   // bytes between variable passes
+    using L = Lane<G, PCM, DCM, PVM, CVM, CMIN, RC, PROF, TAB>;
     static constexpr uint32_t kSlot = 4u * G;         // bytes between a variable's slots
+
+    // shared byte address of slot 0 of this lane's variable at pass p
+    static __device__ __forceinline__ uint32_t pass_base(const L &ln, int p)
+    {
+        return ln.lane_base + 4u * G * (uint32_t)L::off(p);
+    }
 
     // Initial messages of a BP run: every variable announces its prior LLR
     // tagged with its hard decision (cut variables carry lambda = +inf);
@@ -385,19 +440,21 @@ struct Decoder {
                 const uint32_t e = lam <= 0.0f ? 1u : 0u;
                 hd |= e << p;
                 const uint32_t v = (__float_as_uint(lam) & ~1u) | e;
-                const uint32_t base = ln.lane_base + p * kPass;
+                const uint32_t base = pass_base(ln, p);
                 if (RULE == 1 && g.wts) {   // weighted BP: q = clip(wv[0] lambda) per edge
                     const float *wv = g.wts + (size_t)g.w_T * g.slots;
 #pragma unroll
                     for (int m = 0; m < CVM; ++m) {
+                        if (m >= L::cv(p)) continue;
                         const bool on = m < CMIN || ln.has(p, m);
-                        const float q = on ? fminf(fmaxf(__ldg(wv + (p * CVM + m) * G + u) * lam, -g.w_clip), g.w_clip)
+                        const float q = on ? fminf(fmaxf(__ldg(wv + (L::off(p) + m) * G + u) * lam, -g.w_clip), g.w_clip)
                                            : 0.0f;
                         sts32(base + m * kSlot, on ? ((__float_as_uint(q) & ~1u) | e) : 0u);
                     }
                 } else {
 #pragma unroll
-                    for (int m = 0; m < CVM; ++m) sts32(base + m * kSlot, (m < CMIN || ln.has(p, m)) ? v : 0u);
+                    for (int m = 0; m < CVM; ++m)
+                        if (m < L::cv(p)) sts32(base + m * kSlot, (m < CMIN || ln.has(p, m)) ? v : 0u);
                 }
 #ifdef BPDC_CHECKS
                 if (post_row && ((ln.vvalid >> p) & 1u) && !post_ok(g, (long long)p * G + u)) {} else
@@ -406,6 +463,68 @@ struct Decoder {
             }
         }
         return hd & ln.vvalid;
+    }
+
+    // Variable update at pass P (CVP = L::cv(P) slots per variable): the
+    // posterior L = lambda + sum r, the hard decision e = [L <= 0] (Eq. 4) and
+    // the extrinsic messages q = lambda + the other r (prefix and suffix
+    // sums), stored tagged with e; at the last iteration slot 0 keeps the
+    // tagged L for the cut selection.  Slots past a variable's degree hold 0,
+    // so a pass wider than the degree adds exact zeros.  Returns e.
+    template <bool FAST, int P>
+    static __device__ __forceinline__ uint32_t var_pass(const DevGraph &g, const L &ln, int u, int t, bool last,
+                                                        float *post_row)
+    {
+        constexpr int CVP = L::cv(P);
+        const uint32_t base = pass_base(ln, P);
+        float r[CVP];
+#pragma unroll
+        for (int m = 0; m < CVP; ++m) r[m] = __uint_as_float(lds32(base + m * kSlot));
+        float pre[CVP + 1];
+        pre[0] = ln.lamv[P];
+#pragma unroll
+        for (int m = 0; m < CVP; ++m) pre[m + 1] = pre[m] + r[m];
+        float suf[CVP + 1];
+        suf[CVP] = 0.0f;
+        suf[CVP - 1] = r[CVP - 1];
+#pragma unroll
+        for (int m = CVP - 2; m >= 1; --m) suf[m] = r[m] + suf[m + 1];
+        const float Lp = pre[CVP];
+        const uint32_t e = Lp <= 0.0f ? 1u : 0u;
+        const float *wv = (RULE == 1 && g.wts)
+            ? g.wts + ((size_t)g.w_T + min(t + 1, g.w_T) - 1) * g.slots + L::off(P) * G + u
+            : nullptr;
+#pragma unroll
+        for (int m = 0; m < CVP; ++m) {
+            float q = (m == CVP - 1) ? pre[m] : pre[m] + suf[m + 1];
+            if (RULE == 1 && wv) q = fminf(fmaxf(__ldg(wv + m * G) * q, -g.w_clip), g.w_clip);
+            const uint32_t qv = (__float_as_uint(q) & ~1u) | e;
+            if (m < CMIN) sts32(base + m * kSlot, qv);
+            else sts32_if(base + m * kSlot, qv, ln.has(P, m));
+        }
+        if (last) {   // slot 0 keeps L for the cut selection
+            const uint32_t lv = (__float_as_uint(Lp) & ~1u) | e;
+            if (CMIN > 0) sts32(base, lv);
+            else sts32_if(base, lv, ln.has(P, 0));
+        }
+#ifdef BPDC_CHECKS
+        if (!FAST && post_row && ((ln.vvalid >> P) & 1u) && !post_ok(g, (long long)P * G + u)) {} else
+#endif
+        if (!FAST && post_row && ((ln.vvalid >> P) & 1u)) post_row[__ldg(g.pos_col + P * G + u)] = Lp;
+        return e;
+    }
+
+    // The variable updates of passes P .. PVM-1 (all passes of the variant on
+    // the fast path, else those the graph occupies); ORs decision bit p of
+    // each pass into nhd.
+    template <bool FAST, int P>
+    static __device__ __forceinline__ void var_passes(const DevGraph &g, const L &ln, int u, int t, bool last,
+                                                      float *post_row, uint32_t &nhd)
+    {
+        if constexpr (P < PVM) {
+            if (FAST || P < g.pv) nhd |= var_pass<FAST, P>(g, ln, u, t, last, post_row) << P;
+            var_passes<FAST, P + 1>(g, ln, u, t, last, post_row, nhd);
+        }
     }
 
     // One BP run (flooding, normalized min-sum).  The slots must hold the
@@ -475,6 +594,42 @@ struct Decoder {
 #pragma unroll
                             for (int k = 0; k + 1 < DCM; k += 2) gather2(k, k == 0);
                             if (DCM & 1) gather(DCM - 1);
+                        } else if constexpr (L::kTab) {
+                            // the lane's edge word indices come from its shared
+                            // table, 8 per 16-byte load; the two edges of a word
+                            // go through the pairwise minimum (mn1 = mn2 = +inf
+                            // before the first pair gives the first pair's
+                            // order statistics)
+                            auto pair = [&](uint32_t w) {
+                                const float va = ldsf(ln.word_addr(w & 0xFFFFu));
+                                const float vb = ldsf(ln.word_addr(w >> 16));
+                                S ^= __float_as_uint(va) ^ __float_as_uint(vb);
+                                const float lo = fminf(fabsf(va), fabsf(vb)), hi = fmaxf(fabsf(va), fabsf(vb));
+                                mn2 = fmin3(mn2, fmaxf(mn1, lo), hi);
+                                mn1 = fminf(mn1, lo);
+                            };
+                            constexpr int kFull = DCM / kTabEdges, kTail = DCM % kTabEdges;
+#pragma unroll 1
+                            for (int c = 0; c < kFull; ++c) {
+                                const uint4 w = lds128(ln.tab + 16u * G * c);
+                                pair(w.x);
+                                pair(w.y);
+                                pair(w.z);
+                                pair(w.w);
+                            }
+                            if constexpr (kTail > 0) {
+                                const uint4 w = lds128(ln.tab + 16u * G * kFull);
+                                const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                for (int h = 0; h < kTail / 2; ++h) pair(ww[h]);
+                                if constexpr (kTail & 1) {
+                                    const float v = ldsf(ln.word_addr(ww[kTail / 2] & 0xFFFFu));
+                                    S ^= __float_as_uint(v);
+                                    const float av = fabsf(v);
+                                    mn2 = fminf(mn2, fmaxf(mn1, av));
+                                    mn1 = fminf(mn1, av);
+                                }
+                            }
                         } else {   // long rows: bounded unrolling keeps few loads in flight
 #pragma unroll 5
                             for (int k = 0; k < DCM; ++k) gather(k);
@@ -485,8 +640,8 @@ struct Decoder {
                             // holding min1 and min1 for all others; with a tie at
                             // min1 both are equal, so no argmin is needed
                             const uint32_t Sm = S & 0x80000000u;
-                            uint32_t m1 = __float_as_uint(alpha * fminf(mn1, kLlrCap)) ^ Sm;
-                            uint32_t m2 = __float_as_uint(alpha * fminf(mn2, kLlrCap)) ^ Sm;
+                            uint32_t m1 = __float_as_uint(alpha * clamp_min(mn1)) ^ Sm;
+                            uint32_t m2 = __float_as_uint(alpha * clamp_min(mn2)) ^ Sm;
                             if (RC && !live) m1 = m2 = 0x7F800000u;   // idle check: writes +inf back
                             auto put = [&](int k) {
                                 const uint32_t a = ln.addr(p, k);
@@ -501,6 +656,35 @@ struct Decoder {
                             if constexpr (kHold) {
 #pragma unroll
                                 for (int k = 0; k < DCM; ++k) put(k);
+                            } else if constexpr (L::kTab) {
+                                // each q read again from its slot, then overwritten by r
+                                auto put_at = [&](uint32_t a) {
+                                    const float vk = ldsf(a);
+                                    const bool is_min = fabsf(vk) == mn1;
+                                    const uint32_t out = (is_min ? m2 : m1) ^ (__float_as_uint(vk) & 0x80000000u);
+                                    if (RC) sts32(a, out);
+                                    else sts32_if(a, out, a != ln.inf_addr);
+                                };
+                                auto put2 = [&](uint32_t w) {
+                                    put_at(ln.word_addr(w & 0xFFFFu));
+                                    put_at(ln.word_addr(w >> 16));
+                                };
+                                constexpr int kFull = DCM / kTabEdges, kTail = DCM % kTabEdges;
+#pragma unroll 1
+                                for (int c = 0; c < kFull; ++c) {
+                                    const uint4 w = lds128(ln.tab + 16u * G * c);
+                                    put2(w.x);
+                                    put2(w.y);
+                                    put2(w.z);
+                                    put2(w.w);
+                                }
+                                if constexpr (kTail > 0) {
+                                    const uint4 w = lds128(ln.tab + 16u * G * kFull);
+                                    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                    for (int h = 0; h < kTail / 2; ++h) put2(ww[h]);
+                                    if constexpr (kTail & 1) put_at(ln.word_addr(ww[kTail / 2] & 0xFFFFu));
+                                }
                             } else {
 #pragma unroll 5
                                 for (int k = 0; k < DCM; ++k) put(k);
@@ -557,7 +741,7 @@ struct Decoder {
                                 const uint32_t a = ln.addr(p, k);
                                 const bool is_min = fabsf(__uint_as_float(qb[k])) == mn1;
                                 const bool own_b = sb != sa && is_min;
-                                float mag = pair ? (is_min ? mn2 : mn1)
+                                float mag = pair ? clamp_min(is_min ? mn2 : mn1)
                                                  : (own_b ? rb : sa + phi(pre + suf[k + 1]));
                                 mag = fminf(mag, kLlrCap);
                                 pre += f[k];
@@ -581,49 +765,8 @@ struct Decoder {
             if (!grp.any((unsat & 1u) != 0)) { iters = t - 1; return true; }
             if (t > T) { iters = T; return false; }
             // ---- variable phase ----
-            const bool last = t == T;
             uint32_t nhd = 0;
-#pragma unroll
-            for (int p = 0; p < PVM; ++p) {
-                if (FAST || p < g.pv) {
-                    const uint32_t base = ln.lane_base + p * kPass;
-                    float r[CVM];
-#pragma unroll
-                    for (int m = 0; m < CVM; ++m) r[m] = __uint_as_float(lds32(base + m * kSlot));
-                    float pre[CVM + 1];
-                    pre[0] = ln.lamv[p];
-#pragma unroll
-                    for (int m = 0; m < CVM; ++m) pre[m + 1] = pre[m] + r[m];
-                    float suf[CVM + 1];
-                    suf[CVM] = 0.0f;
-                    suf[CVM - 1] = r[CVM - 1];
-#pragma unroll
-                    for (int m = CVM - 2; m >= 1; --m) suf[m] = r[m] + suf[m + 1];
-                    const float Lp = pre[CVM];
-                    const uint32_t e = Lp <= 0.0f ? 1u : 0u;
-                    nhd |= e << p;
-                    const float *wv = (RULE == 1 && g.wts)
-                        ? g.wts + ((size_t)g.w_T + min(t + 1, g.w_T) - 1) * g.slots + (p * CVM) * G + u
-                        : nullptr;
-#pragma unroll
-                    for (int m = 0; m < CVM; ++m) {
-                        float q = (m == CVM - 1) ? pre[m] : pre[m] + suf[m + 1];
-                        if (RULE == 1 && wv) q = fminf(fmaxf(__ldg(wv + m * G) * q, -g.w_clip), g.w_clip);
-                        const uint32_t qv = (__float_as_uint(q) & ~1u) | e;
-                        if (m < CMIN) sts32(base + m * kSlot, qv);
-                        else sts32_if(base + m * kSlot, qv, ln.has(p, m));
-                    }
-                    if (last) {   // slot 0 keeps L for the cut selection
-                        const uint32_t lv = (__float_as_uint(Lp) & ~1u) | e;
-                        if (CMIN > 0) sts32(base, lv);
-                        else sts32_if(base, lv, ln.has(p, 0));
-                    }
-#ifdef BPDC_CHECKS
-                    if (!FAST && post_row && ((ln.vvalid >> p) & 1u) && !post_ok(g, (long long)p * G + u)) {} else
-#endif
-                    if (!FAST && post_row && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = Lp;
-                }
-            }
+            var_passes<FAST, 0>(g, ln, u, t, t == T, post_row, nhd);
             hd = nhd & ln.vvalid;
             grp.sync();
         }
@@ -774,7 +917,7 @@ struct Decoder {
                                 ln.lamv[p] = f_inf();   // Algorithm 2: cut prior 0
                             } else if (g.dc_prior && ln.has(p, 0)) {
                                 // first-run posterior as prior, p_hat clamped to [1e-12, 1/2]
-                                const float Lj = __uint_as_float(__float_as_uint(slot[p * g.cv * G + u]) & ~1u);
+                                const float Lj = __uint_as_float(__float_as_uint(slot[L::off(p) * G + u]) & ~1u);
                                 ln.lamv[p] = fminf(fmaxf(Lj, 0.0f), 27.631021115928547f);
                             }
                         }
@@ -838,7 +981,8 @@ struct Decoder {
     }
 };
 
-template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int RULE, int BLOCK, int MINB>
+template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int RULE, int BLOCK, int MINB,
+          uint64_t PROF, bool TAB>
 __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int region_words)
 {
     extern __shared__ uint32_t smem[];
@@ -857,7 +1001,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int 
         grp.leader = 0;
     }
     uint32_t *region = smem + (size_t)gib * region_words;
-    Decoder<G, PCM, DCM, PVM, CVM, CMIN, RC, RULE>::decode(ld, region, grp, gib);
+    Decoder<G, PCM, DCM, PVM, CVM, CMIN, RC, RULE, PROF, TAB>::decode(ld, region, grp, gib);
 }
 
 // Cut selection alone, one block per shot (same selection code as the fused kernel).
@@ -930,27 +1074,36 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
 // ---------------------------------------------------------------------------
 // Variant table: (id, G, check passes, row weight, variable passes, column
 // weight, minimum column weight, regular rows, check rule (0 min-sum,
-// 1 product-sum), block threads, min blocks per SM).  Variant 13 takes
-// circuit-level detector models (rows of up to 35 edges, ~217 KB of message
-// slots per shot, one shot per SM).
-#define BPDC_VARIANTS(X)                               \
-    X(0, 32, 3, 6, 5, 3, 3, true, 0, 256, 4)           \
-    X(1, 256, 5, 7, 10, 4, 3, true, 0, 256, 3)         \
-    X(2, 512, 3, 7, 5, 4, 3, true, 0, 512, 2)          \
-    X(3, 256, 4, 8, 11, 3, 2, false, 0, 256, 3)        \
-    X(4, 512, 2, 8, 6, 3, 2, false, 0, 512, 2)         \
-    X(5, 32, 4, 8, 8, 4, 1, false, 0, 256, 4)          \
-    X(6, 128, 10, 7, 20, 4, 3, true, 0, 128, 6)        \
-    X(7, 32, 3, 6, 5, 3, 3, true, 0, 256, 3)           \
-    X(8, 256, 5, 7, 10, 4, 3, true, 0, 256, 2)         \
-    X(9, 512, 3, 7, 5, 4, 3, true, 0, 512, 1)          \
-    X(10, 256, 4, 8, 11, 3, 2, false, 0, 256, 2)       \
-    X(11, 32, 4, 4, 4, 2, 1, false, 1, 256, 4)         \
-    X(12, 32, 3, 6, 5, 3, 3, true, 1, 256, 4)          \
-    X(13, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1)
+// 1 product-sum), block threads, min blocks per SM, slots per variable pass
+// (4 bits per pass, 0: the column weight in every pass), shared edge table).
+// Variants 13 and 14 take circuit-level detector models (rows of up to 35
+// edges, one shot per SM): 13 with 6 slots in every pass and the check-edge
+// indices read from global memory at each access, 14 with variables sorted by
+// degree into passes of 6, 5, 4, 3, ... slots (a third less shared memory)
+// and the check-edge indices in a shared-memory table.  Variant 15 is variant
+// 1 (HGP-like graphs) with passes of 4, 4, 4, 4, 3, ... slots: the degree-4
+// variables of a hypergraph product in the first passes.
+#define BPDC_VARIANTS(X)                                                  \
+    X(0, 32, 3, 6, 5, 3, 3, true, 0, 256, 4, 0, false)                    \
+    X(1, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0, false)                  \
+    X(2, 512, 3, 7, 5, 4, 3, true, 0, 512, 2, 0, false)                   \
+    X(3, 256, 4, 8, 11, 3, 2, false, 0, 256, 3, 0, false)                 \
+    X(4, 512, 2, 8, 6, 3, 2, false, 0, 512, 2, 0, false)                  \
+    X(5, 32, 4, 8, 8, 4, 1, false, 0, 256, 4, 0, false)                   \
+    X(6, 128, 10, 7, 20, 4, 3, true, 0, 128, 6, 0, false)                 \
+    X(7, 32, 3, 6, 5, 3, 3, true, 0, 256, 3, 0, false)                    \
+    X(8, 256, 5, 7, 10, 4, 3, true, 0, 256, 2, 0, false)                  \
+    X(9, 512, 3, 7, 5, 4, 3, true, 0, 512, 1, 0, false)                   \
+    X(10, 256, 4, 8, 11, 3, 2, false, 0, 256, 2, 0, false)                \
+    X(11, 32, 4, 4, 4, 2, 1, false, 1, 256, 4, 0, false)                  \
+    X(12, 32, 3, 6, 5, 3, 3, true, 1, 256, 4, 0, false)                   \
+    X(13, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0, false)              \
+    X(14, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0x333333456ull, true)   \
+    X(15, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0x3333334444ull, false)
 
 static const Variant kVariants[] = {
-#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB) {id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB},
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB) \
+    {id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB},
     BPDC_VARIANTS(X)
 #undef X
 };
@@ -976,8 +1129,8 @@ bool check_status(int *, long long *) { return false; }
 static const void *variant_fn(int id)
 {
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB) \
-    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB>;
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB) \
+    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB>;
         BPDC_VARIANTS(X)
 #undef X
     default: return nullptr;
@@ -1026,9 +1179,10 @@ cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_byte
 {
     const int region = smem_bytes / 4 / (kVariants[id].block_threads / kVariants[id].G);
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB)                                                     \
-    case id:                                                                                                  \
-        decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB><<<grid, BLK, smem_bytes, s>>>(ld, region); \
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB)                                \
+    case id:                                                                                        \
+        decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB>                        \
+            <<<grid, BLK, smem_bytes, s>>>(ld, region);                                             \
         return cudaGetLastError();
         BPDC_VARIANTS(X)
 #undef X
@@ -1049,21 +1203,23 @@ static __device__ __align__(256) unsigned char g_static_scratch[256 + kStaticBat
 // Device address of the scratch array on the current device.  In host code
 // the symbol is only a host-side stand-in; the address comes from
 // cudaGetSymbolAddress, resolved once per device with that device current.
+// Calls from several host threads may resolve it at the same time: they store
+// the same value, through atomics.
 static cudaError_t static_scratch_address(void **out)
 {
     constexpr int kMaxDevices = 64;
-    static void *addr[kMaxDevices] = {};
+    static std::atomic<void *> addr[kMaxDevices];
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!addr[dev]) {
-        void *p = nullptr;
+    void *p = addr[dev].load(std::memory_order_acquire);
+    if (!p) {
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
-        addr[dev] = p;
+        addr[dev].store(p, std::memory_order_release);
     }
-    *out = addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

@@ -44,8 +44,11 @@ struct Rng {
     }
 };
 
+// cap: variables per bank.  cap_ge (empty: none): cap_ge[d] is the most
+// variables of degree >= d one bank may hold (its positions in passes with at
+// least d slots).
 void assign_banks(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col,
-                  int cap, std::vector<int> &bank)
+                  int cap, const std::vector<int> &cap_ge, std::vector<int> &bank)
 {
     const int ng = (M + 31) / 32;
     std::vector<int> d(ng, 0);
@@ -62,8 +65,37 @@ void assign_banks(int M, int N, const std::vector<int32_t> &row_ptr, const std::
     std::vector<std::vector<int>> gv(ng);
     for (int i = 0; i < M; ++i)
         for (int a = row_ptr[i]; a < row_ptr[i + 1]; ++a) gv[i / 32].push_back(col[a]);
+    // degree of every variable, and per bank the number of members of degree >= d
+    std::vector<int> deg(N, 0);
+    for (int32_t c : col) deg[c]++;
+    const int dmax = cap_ge.empty() ? 0 : (int)cap_ge.size() - 1;
+    std::vector<int> ge((size_t)32 * (dmax + 1), 0);
     bank.resize(N);
-    for (int j = 0; j < N; ++j) bank[j] = j % 32;
+    if (cap_ge.empty()) {
+        for (int j = 0; j < N; ++j) bank[j] = j % 32;
+    } else {
+        // start balanced: variables in order of decreasing degree, dealt round robin
+        std::vector<int> byd(N);
+        std::iota(byd.begin(), byd.end(), 0);
+        std::stable_sort(byd.begin(), byd.end(), [&](int a, int b) { return deg[a] > deg[b]; });
+        for (int r = 0; r < N; ++r) bank[byd[r]] = r % 32;
+        for (int j = 0; j < N; ++j)
+            for (int d = 1; d <= std::min(deg[j], dmax); ++d) ge[(size_t)bank[j] * (dmax + 1) + d]++;
+    }
+    // j may join bank b (which does not hold it) without a swap
+    auto fits = [&](int j, int b) {
+        for (int d = 1; d <= std::min(deg[j], dmax); ++d)
+            if (ge[(size_t)b * (dmax + 1) + d] + 1 > cap_ge[d]) return false;
+        return true;
+    };
+    // j (in b0) and j2 (in b) may trade banks
+    auto fits_swap = [&](int j, int b0, int j2, int b) {
+        const int lo = std::min(deg[j], deg[j2]), hi = std::min(std::max(deg[j], deg[j2]), dmax);
+        const int gain = deg[j] > deg[j2] ? b : b0;   // the bank that takes the higher degree
+        for (int d = lo + 1; d <= hi; ++d)
+            if (ge[(size_t)gain * (dmax + 1) + d] + 1 > cap_ge[d]) return false;
+        return true;
+    };
     std::vector<int> n((size_t)ng * 32, 0);
     for (int j = 0; j < N; ++j)
         for (auto gc : vg[j]) n[(size_t)gc.first * 32 + bank[j]] += gc.second;
@@ -89,6 +121,10 @@ void assign_banks(int M, int N, const std::vector<int32_t> &row_ptr, const std::
             n[(size_t)gc.first * 32 + b0] -= gc.second;
             n[(size_t)gc.first * 32 + b] += gc.second;
         }
+        for (int d = 1; d <= std::min(deg[j], dmax); ++d) {
+            ge[(size_t)b0 * (dmax + 1) + d]--;
+            ge[(size_t)b * (dmax + 1) + d]++;
+        }
         auto &m0 = members[b0];
         const int last = m0.back();
         m0[slot_in[j]] = last;
@@ -106,13 +142,14 @@ void assign_banks(int M, int N, const std::vector<int32_t> &row_ptr, const std::
         bt = jt = -1;
         for (int b = 0; b < 32; ++b) {
             if (b == b0) continue;
-            if ((int)members[b].size() < cap) {
+            if ((int)members[b].size() < cap && (cap_ge.empty() || fits(j, b))) {
                 const int dl = delta(j, b0, b);
                 if (dl < best || (dl == best && (rng.next() & 1))) { best = dl; bt = b; jt = -1; }
             } else {
                 const auto &mb = members[b];
                 for (int s = 0; s < swaps && !mb.empty(); ++s) {
                     const int j2 = mb[rng.next() % mb.size()];
+                    if (!cap_ge.empty() && !fits_swap(j, b0, j2, b)) continue;
                     const int d1 = delta(j, b0, b);
                     move(j, b0, b);
                     const int d2 = delta(j2, b, b0);
@@ -260,20 +297,21 @@ uint64_t fnv1a(const std::vector<int32_t> &a, uint64_t h)
 }
 
 void plan_layout_uncached(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col,
-                          int G, int npos, int dc, bool optimize, Layout &out);
+                          int G, int npos, int dc, bool optimize, const std::vector<int> &pass_cv, Layout &out);
 
 }  // namespace
 
 void plan_layout(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col, int G,
-                 int npos, int dc, bool optimize, Layout &out)
+                 int npos, int dc, bool optimize, const std::vector<int> &pass_cv, Layout &out)
 {
     if (!optimize || G % 32 != 0) {
-        plan_layout_uncached(M, N, row_ptr, col, G, npos, dc, optimize, out);
+        plan_layout_uncached(M, N, row_ptr, col, G, npos, dc, optimize, pass_cv, out);
         return;
     }
     static std::mutex mu;
     static std::map<LayoutKey, Layout> cache;
-    const LayoutKey key{fnv1a(col, fnv1a(row_ptr, 0xCBF29CE484222325ull)), M, N, G, npos, dc};
+    std::vector<int32_t> pcv(pass_cv.begin(), pass_cv.end());
+    const LayoutKey key{fnv1a(pcv, fnv1a(col, fnv1a(row_ptr, 0xCBF29CE484222325ull))), M, N, G, npos, dc};
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
@@ -282,7 +320,7 @@ void plan_layout(int M, int N, const std::vector<int32_t> &row_ptr, const std::v
             return;
         }
     }
-    plan_layout_uncached(M, N, row_ptr, col, G, npos, dc, optimize, out);
+    plan_layout_uncached(M, N, row_ptr, col, G, npos, dc, optimize, pass_cv, out);
     std::lock_guard<std::mutex> lk(mu);
     if (cache.size() >= 32) cache.clear();
     cache.emplace(key, out);
@@ -291,25 +329,54 @@ void plan_layout(int M, int N, const std::vector<int32_t> &row_ptr, const std::v
 namespace {
 
 void plan_layout_uncached(int M, int N, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col,
-                          int G, int npos, int dc, bool optimize, Layout &out)
+                          int G, int npos, int dc, bool optimize, const std::vector<int> &pass_cv, Layout &out)
 {
     out.pos_of_var.assign(N, -1);
     out.var_at_pos.assign(npos, -1);
     out.edge_round.assign(col.size(), 0);
+    bool uniform_cv = true;
+    for (size_t p = 1; p < pass_cv.size(); ++p) uniform_cv &= pass_cv[p] == pass_cv[0];
     if (!optimize || G % 32 != 0) {
-        for (int j = 0; j < N; ++j) {
-            out.pos_of_var[j] = j;
-            out.var_at_pos[j] = j;
+        // identity placement (in order of decreasing degree under a
+        // non-uniform slot profile) and CSR edge order
+        std::vector<int> order(N);
+        std::iota(order.begin(), order.end(), 0);
+        if (!uniform_cv) {
+            std::vector<int> dg(N, 0);
+            for (int32_t c : col) dg[c]++;
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dg[a] > dg[b]; });
+        }
+        for (int r = 0; r < N; ++r) {
+            out.pos_of_var[order[r]] = r;
+            out.var_at_pos[r] = order[r];
         }
         for (int i = 0; i < M; ++i)
             for (int a = row_ptr[i], k = 0; a < row_ptr[i + 1]; ++a, ++k) out.edge_round[a] = k;
         return;
     }
-    // 1. bank classes
+    // 1. bank classes, under the per-pass slot counts: a bank's k-th position
+    // is k*32 + b, in pass k / (G/32), so a bank may hold (G/32) variables of
+    // degree >= d per pass with at least d slots
+    std::vector<int> deg(N, 0);
+    for (int32_t c : col) deg[c]++;
+    std::vector<int> cap_ge;
+    const bool uniform = uniform_cv;
+    if (!uniform) {
+        const int dmax = *std::max_element(deg.begin(), deg.end());
+        cap_ge.assign((size_t)dmax + 1, 0);
+        for (int d = 0; d <= dmax; ++d)
+            for (int p = 0; p < (int)pass_cv.size() && p * G < npos; ++p)
+                if (pass_cv[p] >= d) cap_ge[d] += G / 32;
+    }
     std::vector<int> bank;
-    assign_banks(M, N, row_ptr, col, npos / 32, bank);
+    assign_banks(M, N, row_ptr, col, npos / 32, cap_ge, bank);
+    // members of each bank in order of decreasing degree (ties by index) take
+    // its positions in order, so higher degrees land in the wider passes
+    std::vector<int> order(N);
+    std::iota(order.begin(), order.end(), 0);
+    if (!uniform) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return deg[a] > deg[b]; });
     std::vector<int> next(32, 0);   // k-th free position of a bank: k*32 + b
-    for (int j = 0; j < N; ++j) {
+    for (int j : order) {
         const int b = bank[j];
         const int pos = next[b]++ * 32 + b;
         out.pos_of_var[j] = pos;

@@ -8,14 +8,17 @@ sampled shots the oracle decodes one by one.
   {0.002 .. 0.010}, 10^6 shots per point, T_iter = 1000 (Sec. IV).
 
 Sampled shot indices are spread over each 10^6-shot range; the counter
-sampler regenerates any shot on the CPU from its global index."""
+sampler regenerates any shot on the CPU from its global index.  Each sampled
+shot is decoded again alone with posterior output (so that a cut set the GPU
+chose differently near a tie-window edge can be checked) and classified by the
+rules of tests/parity.py."""
 import numpy as np
 import pytest
 import torch
 
 import bpdc_inputs as bi
 from bpdc_inputs.sampler import sample_shots, unpack_bits
-from parity import comparable, well_conditioned
+import parity
 
 pytestmark = pytest.mark.gpu
 
@@ -33,32 +36,37 @@ def pkg():
 
 
 def _sampled_parity(pkg, oracle_mod, items, probs, oo, picks_per_point, rng):
-    """items: the decoded batches (outputs on the device); compares the picked
-    shots of each batch with the oracle.  Returns (compared, picked)."""
-    compared = total = 0
+    """items: the decoded batches (outputs on the device).  Picks shots spread
+    over each batch, checks that the GPU sampler produced the CPU sampler's
+    syndromes, decodes each picked shot again on its own (global index kept)
+    with posterior output, checks that it equals the big launch's result, and
+    classifies the picked shots against the oracle (tests/parity.py).
+    Returns the summed class counts."""
+    import torch
+    total = dict.fromkeys(parity.CLASSES, 0)
+    total["B"] = 0
     for it, P in zip(items, probs):
         idx = np.sort(rng.choice(SHOTS, size=picks_per_point, replace=False))
         s = np.array([sample_shots(P, SEED, int(i), 1)[1][0] for i in idx])
-        # the GPU sampler produced the same syndromes
-        gs = unpack_bits(it["syndromes"][torch.as_tensor(idx, device="cuda")].cpu().numpy().view(np.uint32), P.M)
-        assert (gs == s).all()
-        refs = [oracle_mod.decode_batch(P, s[k:k + 1], int(i), oo, want_post=True, want_post1=True)
-                for k, i in enumerate(idx)]
-        ref = {key: np.concatenate([r[key] for r in refs]) for key in refs[0]}
-        wc = np.array([well_conditioned(oracle_mod, P, s[k:k + 1], int(i), oo, refs[k], draws=1)[0]
-                       for k, i in enumerate(idx)])
-        comp = comparable(P, ref, oo.tie_rel) & wc
+        o = np.array([sample_shots(P, SEED, int(i), 1)[2][0] for i in idx])
         sel = torch.as_tensor(idx, device="cuda")
-        st = it["out"]["status"][sel].cpu().numpy()
-        e = unpack_bits(it["out"]["corrections"][sel].cpu().numpy().view(np.uint32), P.N)
-        iters = it["out"]["iterations"][sel].cpu().numpy().view(np.uint32)
-        same = ((st == ref["status"]) & (e == ref["e_hat"]).all(1) & ((iters & 0xFFFF) == ref["iters1"])
-                & ((iters >> 16) == ref["iters2"]))
-        bad = np.nonzero(comp & ~same)[0]
-        assert bad.size == 0, (P.name, idx[bad][:5])
-        compared += int(comp.sum())
-        total += len(idx)
-    return compared, total
+        gs = unpack_bits(it["syndromes"][sel].cpu().numpy().view(np.uint32), P.M)
+        assert (gs == s).all()
+        g = it["graph"]
+        singles = [g.decode(it["syndromes"][int(i):int(i) + 1].contiguous(), int(i), posterior=True) for i in idx]
+        one = {k: torch.cat([x[k] for x in singles]) for k in ("corrections", "status", "logical_flips",
+                                                                "iterations", "posterior_llr")}
+        for k in ("corrections", "status", "logical_flips", "iterations"):
+            assert bool((one[k] == it["out"][k][sel]).all()), (P.name, k)
+        rep = parity.compare(oracle_mod, P, s, 0, oo, parity.gpu_outcome(P, one), offsets=idx, obs=o)
+        sm = parity.summary(rep)
+        assert rep["unmatched_well"] == 0, (P.name, sm)
+        assert rep["posterior"]["failed"] == 0 and rep["posterior"]["inf_mismatch"] == 0, (P.name, sm)
+        for c in parity.CLASSES:
+            total[c] += rep[c]
+        total["B"] += rep["B"]
+    print(total)
+    return total
 
 
 def test_batched_code_capacity_full_size(pkg, oracle_mod):
@@ -80,13 +88,17 @@ def test_batched_code_capacity_full_size(pkg, oracle_mod):
     torch.cuda.synchronize()
     rng = np.random.default_rng(17)
     oo = oracle_mod.Options(alpha=0.625, max_iter=50)
-    picks = [60 if "hgp" in P.name else 150 for P in probs]
-    compared = total = 0
-    for it, P, k in zip(items, probs, picks):
-        c, t = _sampled_parity(pkg, oracle_mod, [it], [P], oo, k, rng)
-        compared += c
-        total += t
-    assert compared >= 0.5 * total, (compared, total)
+    total = dict.fromkeys(parity.CLASSES, 0)
+    total["B"] = 0
+    for it, P in zip(items, probs):
+        rep = _sampled_parity(pkg, oracle_mod, [it], [P], oo, 60 if "hgp" in P.name else 150, rng)
+        for k in total:
+            total[k] += rep[k]
+    print(total)
+    # compared: outside the |L| < 1e-3 exemption (HGP at p >= 0.09 ends
+    # failed runs with such values on about a quarter of its shots)
+    assert total["B"] - total["exempt_llr"] >= 0.9 * total["B"], total
+    assert total["unmatched_ill"] <= 0.02 * total["B"], total
 
 
 def test_phenomenological_full_size(pkg, oracle_mod):
@@ -101,5 +113,6 @@ def test_phenomenological_full_size(pkg, oracle_mod):
     torch.cuda.synchronize()
     rng = np.random.default_rng(18)
     oo = oracle_mod.Options(alpha=0.625, max_iter=1000)
-    compared, total = _sampled_parity(pkg, oracle_mod, items, probs, oo, 40, rng)
-    assert compared >= 0.5 * total, (compared, total)
+    total = _sampled_parity(pkg, oracle_mod, items, probs, oo, 40, rng)
+    assert total["B"] - total["exempt_llr"] >= 0.95 * total["B"], total
+    assert total["unmatched_ill"] <= 0.02 * total["B"], total

@@ -1,16 +1,29 @@
 """GPU parity: the CUDA decoder, called through the C-ABI, against the FP64
-oracle on the same seeded shots (acceptance rules in tests/parity.py)."""
+oracle on the same seeded shots (acceptance rules and their calibration in
+tests/parity.py and tests/test_parity_acceptance.py).
+
+Every case decodes twice, through the production launch (no posterior) and
+with posterior output (the guarded path), asserts that both give identical
+outcomes, and classifies every shot.  Each case asserts: no well-conditioned
+mismatch; at most MAX_ILL of the shots decided differently where the oracle's
+own outcome changes under rounding-sized prior perturbations; at least
+`min_compared` of the shots outside the |L| < 1e-3 exemption (0.8 unless the
+case states the measured reason); failure counts within two binomial sigma;
+every posterior entry within 1e-4 relative or, where the oracle amplifies
+rounding beyond that, within twice the oracle's own spread."""
 import numpy as np
 import pytest
 
 import bpdc_inputs as bi
+import parity
 from bpdc_inputs.sampler import sample_shots, syndromes, unpack_bits
-from parity import (compare, comparable, from_dev, robust_rows, to_dev, well_conditioned,
-                    within_2_sigma)
+from parity import from_dev, to_dev, within_2_sigma
 
 pytestmark = pytest.mark.gpu
 
 SEED = 0x2510086950
+MAX_ILL = 0.02
+OUTCOME_KEYS = ("corrections", "status", "logical_flips", "iterations")
 
 
 @pytest.fixture(scope="module")
@@ -28,28 +41,42 @@ def pkg(torch_cuda):
     return pkg
 
 
-def _run(pkg, oracle_mod, P, B, opts_kw, seed=SEED, offset=0, G=None, persistent=True):
+def oracle_options(oracle_mod, opts):
+    return oracle_mod.Options(variant=opts.variant, alpha=opts.ms_scale, max_iter=opts.max_iter,
+                              dc_enable=opts.dc_enable, dc_prior=opts.dc_prior, tie_rel=opts.tie_rel,
+                              tie_seed=opts.tie_seed)
+
+
+def _run(pkg, oracle_mod, P, B, opts_kw, seed=SEED, offset=0, G=None, persistent=True, kernel=None):
+    """Decodes B seeded shots both ways and classifies them against the oracle."""
     _, s, o = sample_shots(P, seed, offset, B)
     opts = pkg.Options(**opts_kw)
     g = pkg.Graph.from_problem(P, opts)
     if G:
         g.set_plan(G)
-    out = g.decode(to_dev(s), offset, obs_true=to_dev(o), persistent=persistent)
+    if kernel is not None:
+        g.set_kernel(kernel)
+    fast = g.decode(to_dev(s), offset, obs_true=to_dev(o), persistent=persistent)
+    out = g.decode(to_dev(s), offset, obs_true=to_dev(o), persistent=persistent, posterior=True)
     g.sync_status()
-    oo = oracle_mod.Options(variant=opts.variant, alpha=opts.ms_scale, max_iter=opts.max_iter,
-                            dc_enable=opts.dc_enable, dc_prior=opts.dc_prior, tie_rel=opts.tie_rel,
-                            tie_seed=opts.tie_seed)
-    ref = oracle_mod.decode_batch(P, s, offset, oo, want_post=True, want_post1=True, want_cut=True)
-    ref["well_conditioned"] = well_conditioned(oracle_mod, P, s, offset, oo, ref)
-    return g, s, o, out, ref
+    for k in OUTCOME_KEYS:
+        assert bool((fast[k] == out[k]).all()), f"production and posterior paths differ in {k}"
+    rep = parity.compare(oracle_mod, P, s, offset, oracle_options(oracle_mod, opts),
+                         parity.gpu_outcome(P, out), obs=o)
+    return g, rep
 
 
-def _assert_parity(P, out, ref, o, tie_rel, min_comparable=0.9):
-    rep = compare(P, out, ref, o, tie_rel)
-    print({k: v for k, v in rep.items() if k != "mismatched"})
-    assert rep["comparable"] >= min_comparable * rep["B"], rep
-    assert len(rep["mismatched"]) == 0, (rep, rep["mismatched"][:20])
-    assert within_2_sigma(rep["fail_gpu"], rep["fail_ref"], rep["B"]), rep
+def _assert_parity(rep, min_compared=0.8, max_ill=MAX_ILL):
+    sm = parity.summary(rep)
+    print(sm)
+    B = rep["B"]
+    assert rep["unmatched_well"] == 0, sm
+    assert rep["unmatched_ill"] <= max_ill * B, sm
+    assert rep["compared"] >= min_compared * B, sm
+    assert within_2_sigma(rep["fail_gpu"], rep["fail_ref"], B), sm
+    post = rep.get("posterior")
+    if post is not None:
+        assert post["failed"] == 0 and post["inf_mismatch"] == 0, post
     return rep
 
 
@@ -75,56 +102,81 @@ def test_gpu_sampler_bit_exact(pkg, name):
 def test_cfg_bb72_code_capacity_parity(pkg, oracle_mod):
     """BB [[72,12,6]], p = 0.05, 10^4 shots, alpha = 0.625, T_iter = 50."""
     P = bi.bb_problem("bb72", 0.05)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 10000, dict(ms_scale=0.625, max_iter=50))
-    rep = _assert_parity(P, out, ref, o, 1e-5)
+    g, rep = _run(pkg, oracle_mod, P, 10000, dict(ms_scale=0.625, max_iter=50))
+    _assert_parity(rep, min_compared=0.99)
     assert rep["status_ref"][1] > 50 and rep["status_ref"][2] > 50
+    assert rep["posterior"]["shots_by_status"][1] > 100   # posteriors after the cut
 
 
-@pytest.mark.parametrize("G", [32])
-def test_bb144_parity_every_small_plan(pkg, oracle_mod, G):
+def test_bb144_parity(pkg, oracle_mod):
     P = bi.bb_problem("bb144", 0.06)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 3000, dict(ms_scale=0.625, max_iter=50), G=G)
-    assert g.info["threads_per_shot"] == G
-    _assert_parity(P, out, ref, o, 1e-5)
+    g, rep = _run(pkg, oracle_mod, P, 3000, dict(ms_scale=0.625, max_iter=50), G=32)
+    assert g.info["threads_per_shot"] == 32
+    _assert_parity(rep, min_compared=0.99)
 
 
-@pytest.mark.parametrize("G", [128, 256, 512])
-def test_hgp_parity(pkg, oracle_mod, G):
+@pytest.mark.parametrize("p,min_compared", [(0.03, 0.99), (0.06, 0.95), (0.09, 0.7)])
+def test_hgp_parity(pkg, oracle_mod, p, min_compared):
+    """HGP-2500 (the dominant graph of the batched workload), 3000 shots per p,
+    the automatic kernel.  At p = 0.09 every shot fails and about 28 % of the
+    failed runs end with some |L_j| < 1e-3 among the 2500 posteriors: those
+    shots are exempt from bit-exactness, the rest must match."""
+    P = bi.hgp_problem(p)
+    g, rep = _run(pkg, oracle_mod, P, 3000, dict(ms_scale=0.625, max_iter=50))
+    _assert_parity(rep, min_compared=min_compared)
+    if p == 0.03:
+        assert rep["same_cut"] > 100   # the cut-set path is exercised
+
+
+@pytest.mark.parametrize("G", [128, 512])
+def test_hgp_parity_other_group_sizes(pkg, oracle_mod, G):
     P = bi.hgp_problem(0.06)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 600, dict(ms_scale=0.625, max_iter=50), G=G)
-    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.4)
+    g, rep = _run(pkg, oracle_mod, P, 1000, dict(ms_scale=0.625, max_iter=50), G=G)
+    assert g.info["threads_per_shot"] == G
+    _assert_parity(rep, min_compared=0.95)
 
 
 def test_phenomenological_parity_512(pkg, oracle_mod):
     P = bi.phenomenological_bb_problem("bb72", 6, 0.02)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 600, dict(ms_scale=0.625, max_iter=100), G=512)
-    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.5)
+    g, rep = _run(pkg, oracle_mod, P, 600, dict(ms_scale=0.625, max_iter=100), G=512)
+    _assert_parity(rep, min_compared=0.99)
 
 
-def test_phenomenological_parity(pkg, oracle_mod):
-    P = bi.phenomenological_bb_problem("bb144", 12, 0.006)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 300, dict(ms_scale=0.625, max_iter=200))
-    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.8)
+@pytest.mark.parametrize("p,T,B", [(0.006, 200, 400), (0.010, 1000, 600)])
+def test_phenomenological_parity(pkg, oracle_mod, p, T, B):
+    """Phenomenological BB[[144,12,12]], 12 noisy rounds + 1 perfect; the
+    second case has the workload's p = q = 0.01 and T_iter = 1000."""
+    P = bi.phenomenological_bb_problem("bb144", 12, p)
+    g, rep = _run(pkg, oracle_mod, P, B, dict(ms_scale=0.625, max_iter=T))
+    _assert_parity(rep, min_compared=0.99)
 
 
 def test_posterior_prior_parity(pkg, oracle_mod):
-    """Second BP on the first-run posterior (Algorithm 1 as printed)."""
+    """Second BP on the first-run posterior (Algorithm 1 as printed).  Every
+    variable with L <= 0 after the first run gets prior LLR 0, so the second
+    run is full of exact ties; about 1.3 % of the shots are decided by
+    rounding there (unmatched_ill, bounded at 2 %)."""
     P = bi.bb_problem("bb72", 0.06)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, dict(ms_scale=0.625, max_iter=40, dc_prior=1))
-    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.8)
+    g, rep = _run(pkg, oracle_mod, P, 4000, dict(ms_scale=0.625, max_iter=40, dc_prior=1))
+    _assert_parity(rep, min_compared=0.99)
 
 
 def test_alpha_one_parity(pkg, oracle_mod):
-    """Plain min-sum (alpha = 1) on uniform priors keeps exact symmetric ties in
-    exact-tie arithmetic; the FP64 oracle then fails twice as often as under a
-    1e-9 relative perturbation of the priors, and FP32 rounding acts like such
-    a perturbation.  Bit-exactness is required on the well-conditioned shots;
-    the failure statistics are compared with the perturbed oracle."""
+    """Plain min-sum (alpha = 1) on uniform priors keeps exact symmetric ties
+    in exact-tie arithmetic: about 60 % of the shots end with some L_j = 0
+    (exempt), and the FP64 oracle fails twice as often as under a 1e-9
+    relative perturbation of the priors; FP32 rounding acts like such a
+    perturbation.  Bit-exactness on the shots the oracle decides stably;
+    unmatched rounding-decided shots bounded at 8 %; failure statistics against
+    the perturbed oracle."""
     P = bi.bb_problem("bb72", 0.06)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, dict(ms_scale=1.0, max_iter=72))
-    rep = compare(P, out, ref, o, 1e-5)
-    print({k: v for k, v in rep.items() if k != "mismatched"})
-    assert rep["comparable"] >= 0.05 * rep["B"] and len(rep["mismatched"]) == 0, rep
+    g, rep = _run(pkg, oracle_mod, P, 4000, dict(ms_scale=1.0, max_iter=72))
+    sm = parity.summary(rep)
+    print(sm)
+    assert rep["unmatched_well"] == 0 and rep["unmatched_ill"] <= 0.08 * rep["B"], sm
+    assert rep["compared"] >= 0.35 * rep["B"], sm
+    assert rep["posterior"]["failed"] == 0, sm
+    _, s, o = sample_shots(P, SEED, 0, 4000)
     rng = np.random.default_rng(5)
     Q = P.with_priors(P.priors * (1 + 1e-9 * rng.standard_normal(P.N)))
     pert = oracle_mod.decode_batch(Q, s, 0, oracle_mod.Options(alpha=1.0, max_iter=72))
@@ -135,50 +187,36 @@ def test_alpha_one_parity(pkg, oracle_mod):
 @pytest.mark.parametrize("d,p,prior", [(7, 0.01, 1), (7, 0.05, 1), (5, 0.06, 0)])
 def test_surface_code_product_sum_parity(pkg, oracle_mod, d, p, prior):
     """The paper's surface-code setting: product-sum BP, T_iter = n, second BP
-    on the first-run posterior (Sec. III.B)."""
+    on the first-run posterior (Sec. III.B).  Weight-2 boundary checks give
+    exact posterior zeros (|L| < 1e-3, exempt) on 4 % (d = 7, p = 0.05) to
+    17 % (d = 5, p = 0.06) of the shots."""
     P = bi.surface_problem(d, p)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 6000, dict(variant=1, max_iter=d * d, dc_prior=prior))
+    g, rep = _run(pkg, oracle_mod, P, 6000, dict(variant=1, max_iter=d * d, dc_prior=prior))
     assert g.info["kernel_id"] == 11
-    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.5)
+    _assert_parity(rep, min_compared=0.8)
 
 
 def test_bb72_product_sum_parity(pkg, oracle_mod):
     P = bi.bb_problem("bb72", 0.05)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, dict(variant=1, max_iter=50))
+    g, rep = _run(pkg, oracle_mod, P, 4000, dict(variant=1, max_iter=50))
     assert g.info["kernel_id"] == 12
-    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.8)
+    _assert_parity(rep, min_compared=0.99)
 
 
 def test_surface_code_min_sum_parity(pkg, oracle_mod):
     P = bi.surface_problem(7, 0.04)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 4000, dict(ms_scale=0.625, max_iter=49, dc_prior=1))
-    _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.5)
-
-
-def test_product_sum_posteriors(pkg, oracle_mod):
-    P = bi.surface_problem(7, 0.03)
-    _, s, _ = sample_shots(P, SEED + 9, 0, 3000)
-    g = pkg.Graph.from_problem(P, pkg.Options(variant=1, max_iter=49, dc_prior=1))
-    out = g.decode(to_dev(s), 0, posterior=True)
-    oo = oracle_mod.Options(variant=1, max_iter=49, dc_prior=1)
-    ref = oracle_mod.decode_batch(P, s, 0, oo, want_post=True, want_post1=True)
-    ref["well_conditioned"] = well_conditioned(oracle_mod, P, s, 0, oo, ref)
-    comp = comparable(P, ref, 1e-5) & ref["well_conditioned"] & (ref["status"] == 0)
-    assert comp.sum() > 1000
-    rp, gp = ref["post"][comp], out["posterior_llr"].cpu().numpy().astype(np.float64)[comp]
-    inf = np.isinf(rp)
-    assert (np.isinf(gp) == inf).all()
-    with np.errstate(invalid="ignore"):
-        rel = np.where(inf, 0.0, np.abs(gp - rp) / np.maximum(np.abs(np.where(inf, 1.0, rp)), 1.0))
-    worst = [(int(np.nonzero(comp)[0][b]), int(j), float(gp[b, j]), float(rp[b, j]))
-             for b, j in np.argwhere(rel > 1e-4)[:5]]
-    assert rel.max() < 1e-4, (rel.max(), worst)
+    g, rep = _run(pkg, oracle_mod, P, 4000, dict(ms_scale=0.625, max_iter=49, dc_prior=1))
+    _assert_parity(rep, min_compared=0.99)
 
 
 # ---------------------------------------------------------------------------
 # single steps
 
 def test_cut_select_matches_oracle(pkg, oracle_mod, torch_cuda):
+    """The selection step of Algorithm 1 alone, on the oracle's first-run
+    posteriors rounded to FP32: every GPU cut set is one the rule makes when
+    values within 1e-6 of a tie-window edge may fall either way, and nearly
+    all equal the oracle's."""
     torch = torch_cuda
     P = bi.bb_problem("bb144", 0.07)
     _, s, _ = sample_shots(P, SEED + 3, 0, 3000)
@@ -188,14 +226,14 @@ def test_cut_select_matches_oracle(pkg, oracle_mod, torch_cuda):
     post = ref["post1"][idx].astype(np.float32)
     g = pkg.Graph.from_problem(P)
     # shot offsets must match the oracle's (global index = position in the batch)
-    cuts = []
+    same = 0
     for k, b in enumerate(idx):
-        c = g.cut_select(torch.from_numpy(post[k][None, :]).cuda(), int(b))
-        cuts.append(from_dev(c, P.N)[0])
-    cuts = np.array(cuts)
-    ok = robust_rows(P.D, ref["post1"][idx], 1e-5)
-    assert ok.mean() > 0.8
-    assert (cuts[ok] == ref["cut"][idx][ok]).all()
+        cut = from_dev(g.cut_select(torch.from_numpy(post[k][None, :]).cuda(), int(b)), P.N)[0]
+        win = parity.possible_winners(P.D, post[k].astype(np.float64), 1e-5, 1e-6, int(b), 0x2510086950,
+                                      oracle_mod.hash64)
+        assert win is not None and parity.cut_is_possible(win, cut), b
+        same += int((cut == ref["cut"][b]).all())
+    assert same >= 0.95 * idx.size, (same, idx.size)
 
 
 def test_bp_on_given_cut_matches_oracle(pkg, oracle_mod):
@@ -356,26 +394,6 @@ def test_edge_cases(pkg, oracle_mod, torch_cuda):
     assert (syndromes(e[st < 2], P.H) == s2[st < 2]).all()
 
 
-def test_posterior_output(pkg, oracle_mod):
-    P = bi.bb_problem("bb72", 0.05)
-    _, s, _ = sample_shots(P, SEED + 8, 0, 3000)
-    g = pkg.Graph.from_problem(P)
-    out = g.decode(to_dev(s), 0, posterior=True)
-    ref = oracle_mod.decode_batch(P, s, 0, oracle_mod.Options(), want_post=True, want_post1=True)
-    post = out["posterior_llr"].cpu().numpy().astype(np.float64)
-    comp = comparable(P, ref, 1e-5) & (ref["status"] == 0)
-    rp = ref["post"][comp]
-    gp = post[comp]
-    assert comp.sum() > 1000
-    inf = np.isinf(rp)
-    assert (np.isinf(gp) == inf).all()
-    with np.errstate(invalid="ignore"):
-        rel = np.where(inf, 0.0, np.abs(gp - rp) / np.maximum(np.abs(np.where(inf, 1.0, rp)), 1.0))
-    worst = [(int(np.nonzero(comp)[0][b]), int(j), float(gp[b, j]), float(rp[b, j]))
-             for b, j in np.argwhere(rel > 1e-4)[:5]]
-    assert rel.max() < 1e-4, (rel.max(), worst)
-
-
 def test_smem_peak_microbenchmark(pkg):
     """The roof the bench divides by: conflict-free 4-byte shared-memory
     traffic moves at most 128 B per SM clock (32 banks x 4 B); GB300 SMs run
@@ -388,47 +406,49 @@ def test_smem_peak_microbenchmark(pkg):
 
 
 # ---------------------------------------------------------------------------
-# circuit-level detector error models (Appendix C / D; kernel 13)
+# circuit-level detector error models (Appendix C / D; kernels 13 and 14)
 
-def test_circuit_level_parity_bb72(pkg, oracle_mod):
+@pytest.mark.parametrize("kernel", [14, 13])
+def test_circuit_level_parity_bb72(pkg, oracle_mod, kernel):
     """BB[[72,12,6]], 6 noisy rounds, p = 2e-3: H_DCM 252 x 2232 with rows of
     up to 35 edges, H_DDM for w = 3, T_iter = 1000 (Sec. IV), priors p for
-    the second BP."""
+    the second BP; both circuit-level kernels (14: degree-sorted passes and a
+    shared edge table, the automatic choice; 13: uniform passes)."""
     from bpdc_inputs import circuit
     P = circuit.circuit_level_problem("bb72", 6, 2e-3)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 400, dict(ms_scale=0.625, max_iter=1000))
-    assert g.info["kernel_id"] == 13
-    rep = _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.6)
+    g, rep = _run(pkg, oracle_mod, P, 400, dict(ms_scale=0.625, max_iter=1000), kernel=kernel)
+    assert g.info["kernel_id"] == kernel
+    _assert_parity(rep, min_compared=0.99)
     assert rep["status_ref"][1] > 20
 
 
 def test_circuit_level_parity_bb144_full_size(pkg, oracle_mod):
     """The circuit-level serving model at full size: BB[[144,12,12]], 12
-    rounds, p = 1e-3 (H_DCM 936 x 8784), on a sample of shots at global
-    offsets spread over a 10^6-shot range, in the launch the server uses."""
+    rounds, p = 1e-3 (H_DCM 936 x 8784), on shots at global offsets spread
+    over a 10^6-shot range, in the multi-batch launch the server uses."""
+    import torch
     from bpdc_inputs import circuit
     P = circuit.circuit_level_problem("bb144", 12, 1e-3)
     opts = pkg.Options(ms_scale=0.625, max_iter=1000)
     g = pkg.Graph.from_problem(P, opts)
-    assert g.info["kernel_id"] == 13
-    offs = [0, 333_333, 999_900]
-    s = np.concatenate([sample_shots(P, SEED + 20, off, 50)[1] for off in offs])
-    o = np.concatenate([sample_shots(P, SEED + 20, off, 50)[2] for off in offs])
-    items = [dict(graph=g, syndromes=to_dev(s[i * 50:(i + 1) * 50]), shot_offset=off,
-                  obs_true=to_dev(o[i * 50:(i + 1) * 50]), out=g.alloc_outputs(50))
-             for i, off in enumerate(offs)]
-    pkg.decode_multi(items)      # one persistent launch over the three batches
-    g.sync_status()
-    import torch
-    out = {k: torch.cat([it["out"][k] for it in items]) for k in items[0]["out"]}
-    oo = oracle_mod.Options(alpha=0.625, max_iter=1000)
-    refs = [oracle_mod.decode_batch(P, s[i * 50:(i + 1) * 50], off, oo, want_post=True, want_post1=True)
-            for i, off in enumerate(offs)]
-    ref = {k: np.concatenate([r[k] for r in refs]) for k in refs[0]}
-    wc = [well_conditioned(oracle_mod, P, s[i * 50:(i + 1) * 50], off, oo, refs[i], draws=1)
-          for i, off in enumerate(offs)]
-    ref["well_conditioned"] = np.concatenate(wc)
-    rep = _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.4)
+    assert g.info["kernel_id"] == 14
+    offs, n = [0, 333_333, 999_900], 70
+    s = np.concatenate([sample_shots(P, SEED + 20, off, n)[1] for off in offs])
+    o = np.concatenate([sample_shots(P, SEED + 20, off, n)[2] for off in offs])
+    outs = {}
+    for post in (False, True):
+        items = [dict(graph=g, syndromes=to_dev(s[i * n:(i + 1) * n]), shot_offset=off,
+                      obs_true=to_dev(o[i * n:(i + 1) * n]), out=g.alloc_outputs(n, posterior=post))
+                 for i, off in enumerate(offs)]
+        pkg.decode_multi(items)      # one persistent launch over the three batches
+        g.sync_status()
+        outs[post] = {k: torch.cat([it["out"][k] for it in items]) for k in items[0]["out"]}
+    for k in OUTCOME_KEYS:
+        assert bool((outs[False][k] == outs[True][k]).all()), k
+    gidx = np.concatenate([np.arange(off, off + n) for off in offs])
+    rep = parity.compare(oracle_mod, P, s, 0, oracle_options(oracle_mod, opts), parity.gpu_outcome(P, outs[True]),
+                         offsets=gidx, obs=o)
+    _assert_parity(rep, min_compared=0.99)
     assert rep["status_ref"][1] > 10
 
 
@@ -437,7 +457,7 @@ def test_circuit_level_parity_bb72_w5(pkg, oracle_mod):
     (App. D; the paper's circuit-level setting): 60 696 rows on BB72, 6 rounds."""
     from bpdc_inputs import circuit
     P = circuit.circuit_level_problem("bb72", 6, 3e-3, w=5)
-    g, s, o, out, ref = _run(pkg, oracle_mod, P, 300, dict(ms_scale=0.625, max_iter=1000))
-    assert g.info["kernel_id"] == 13 and P.D.shape[0] > 50000
-    rep = _assert_parity(P, out, ref, o, 1e-5, min_comparable=0.5)
+    g, rep = _run(pkg, oracle_mod, P, 300, dict(ms_scale=0.625, max_iter=1000))
+    assert g.info["kernel_id"] == 14 and P.D.shape[0] > 50000
+    _assert_parity(rep, min_compared=0.99)
     assert rep["status_ref"][1] > 20
