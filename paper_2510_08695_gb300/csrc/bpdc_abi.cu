@@ -241,10 +241,9 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     // indices in shared memory after the group's other words (16-byte entries)
     const int tab_chunks = (std::max(v.dc_max, P.dc) + kTabEdges - 1) / kTabEdges;
     P.tab_off = 0;
-    if (v.tab) {   // one check pass per lane (the table holds one row per lane)
-        if (v.pc_max != 1) return false;
+    if (v.tab) {   // one 16-byte entry per 8 edges of every check pass of a lane
         P.tab_off = region;
-        region += tab_chunks * G * 4;
+        region += P.pc * tab_chunks * G * 4;
     }
     P.region = region;
     // check edges are kept as 16-bit values in the kernels: byte addresses
@@ -296,13 +295,14 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
                     if (e != kNoEdge) P.chk_word[((size_t)p * dcw + k) * G + u] = (uint16_t)(12 + e);
                 }
         if (v.tab) {
-            // 8 edges of one lane per 16-byte entry: entry (c, u) holds edges
-            // 8c .. 8c+7 of lane u (one check pass), padded with the +inf word
-            P.chk_tab.assign((size_t)tab_chunks * G * kTabEdges, (uint16_t)2);
-            for (int k = 0; k < std::min(dcw, tab_chunks * kTabEdges); ++k)
-                for (int u = 0; u < G; ++u)
-                    P.chk_tab[((size_t)(k / kTabEdges) * G + u) * kTabEdges + k % kTabEdges] =
-                        P.chk_word[(size_t)k * G + u];
+            // 8 edges of one lane per 16-byte entry: entry (p, c, u) holds edges
+            // 8c .. 8c+7 of lane u at check pass p, padded with the +inf word
+            P.chk_tab.assign((size_t)P.pc * tab_chunks * G * kTabEdges, (uint16_t)2);
+            for (int p = 0; p < P.pc; ++p)
+                for (int k = 0; k < std::min(dcw, tab_chunks * kTabEdges); ++k)
+                    for (int u = 0; u < G; ++u)
+                        P.chk_tab[(((size_t)p * tab_chunks + k / kTabEdges) * G + u) * kTabEdges + k % kTabEdges] =
+                            P.chk_word[((size_t)p * dcw + k) * G + u];
         }
     }
     P.var_deg.assign((size_t)npos, 0xFF);   // 0xFF: no variable at this position
@@ -368,7 +368,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     // automatic preference: one warp per shot for small graphs (3 blocks per
     // SM before 4: the same speed with fewer spills), then the 256- and
     // 512-thread groups
-    static const int kOrder[] = {7, 0, 12, 5, 11, 1, 15, 3, 2, 4, 6, 14, 13};
+    static const int kOrder[] = {7, 0, 12, 5, 11, 1, 15, 3, 2, 4, 6, 16, 14, 13};
     Packed P{};
     int vid = -1;
     for (int id : kOrder) {

@@ -15,12 +15,12 @@ constexpr uint16_t kNoEdge = 0xFFFF;
 // Limits of the compiled kernel variants.
 constexpr int kMaxDRowWeight = 64;
 
-// Message slots per variable pass.  A variant's profile holds 4 bits per pass
-// (pass p in bits 4p .. 4p+3, a non-increasing sequence): pass p gives each of
-// its variables prof_cv slots, so that a graph whose variables are sorted by
-// degree into the passes stores no padding for the long tail of low-degree
-// columns.  Profile 0: every pass has cv slots.
-constexpr int prof_cv(uint64_t prof, int cv, int p) { return prof ? (int)((prof >> (4 * p)) & 0xFu) : cv; }
+// Message slots per variable pass.  A variant's profile holds 3 bits per pass
+// (pass p in bits 3p .. 3p+2, a non-increasing sequence, up to 21 passes):
+// pass p gives each of its variables prof_cv slots, so that a graph whose
+// variables are sorted by degree into the passes stores no padding for the
+// long tail of low-degree columns.  Profile 0: every pass has cv slots.
+constexpr int prof_cv(uint64_t prof, int cv, int p) { return prof ? (int)((prof >> (3 * p)) & 0x7u) : cv; }
 // Slots of the passes before p (per lane).
 constexpr int prof_off(uint64_t prof, int cv, int p)
 {
@@ -70,9 +70,10 @@ struct DevGraph {
     const uint16_t *chk_word;    // [pc][variant row width][G] the same as word indices of the group's
                                  // region (the +inf word, 2, for none and for padding): read per
                                  // access by the wide kernels
-    const uint4 *chk_tab;        // [ceil(row width / 8)][G] the same word indices, 8 per entry (edge
-                                 // 8c + e of lane u in 16-bit half e of entry (c, u)): copied into
-                                 // shared memory by the wide kernels with an edge table
+    const uint4 *chk_tab;        // [pc][ceil(row width / 8)][G] the same word indices, 8 per entry
+                                 // (edge 8c + e of lane u at pass p in 16-bit half e of entry
+                                 // (p, c, u)): copied into shared memory by the wide kernels with an
+                                 // edge table
     int32_t tab_off;             // word offset of that shared copy inside the group's region
     const uint8_t *var_deg;      // [pv][G] degree of the variable (0 past N)
     const float *lam;            // [pv][G] prior LLR ln((1-p)/p)

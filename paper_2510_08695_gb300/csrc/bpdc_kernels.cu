@@ -280,10 +280,20 @@ struct Lane {
 
     static constexpr bool kWide = wide_slots(G, kSlotsPerLane);
     // wide form with the check-edge word indices in shared memory: 16-byte
-    // entries of 8 indices, entry c of this lane at tab + 16 * c * G
+    // entries of 8 indices, entry c of pass p of this lane at
+    // tab + 16 * (p * kTabChunks + c) * G
     static constexpr bool kTab = kWide && TAB;
     static constexpr int kTabChunks = (DCM + kTabEdges - 1) / kTabEdges;
-    static_assert(!kTab || (PCM == 1 && kTabChunks > 0), "the shared edge table holds one check pass");
+    static_assert(!kTab || kTabChunks > 0, "a shared edge table needs rows");
+    // rows longer than 16 keep the gathered q in registers for the scatter
+    // when a thread has the registers for it (512 threads or fewer per SM);
+    // else the scatter reads each q again
+    static constexpr bool kHoldLong = kTab && G <= 512;
+
+    __device__ __forceinline__ uint32_t tab_entry(int p, int c) const
+    {
+        return tab + 16u * G * (uint32_t)(p * kTabChunks + c);
+    }
     // shared byte address of each check edge's slot (the +inf word if none):
     // one register per edge when a lane has at most 40 check edges (no
     // unpacking at each access), else two 16-bit values per register.  The
@@ -358,13 +368,18 @@ struct Lane {
             // this lane's entries of the edge table into shared memory; only
             // this lane reads them back, so no barrier is needed
 #pragma unroll
-            for (int c = 0; c < kTabChunks; ++c) {
-                const uint4 e = __ldg(g.chk_tab + (size_t)c * G + u);
+            for (int p = 0; p < PCM; ++p) {
+                if (p >= g.pc) break;
+#pragma unroll
+                for (int c = 0; c < kTabChunks; ++c) {
+                    const uint4 e = __ldg(g.chk_tab + ((size_t)p * kTabChunks + c) * G + u);
+                    const uint32_t a = tab_entry(p, c);
 #ifdef BPDC_CHECKS
-                if (!smem_ok(tab + 16u * c * G, 2) || !smem_ok(tab + 16u * c * G + 12u, 2)) continue;
+                    if (!smem_ok(a, 2) || !smem_ok(a + 12u, 2)) continue;
 #endif
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tab + 16u * c * G), "r"(e.x),
-                             "r"(e.y), "r"(e.z), "r"(e.w));
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(e.x), "r"(e.y), "r"(e.z),
+                                 "r"(e.w));
+                }
             }
         }
 #ifdef BPDC_CHECKS
@@ -563,6 +578,7 @@ struct Decoder {
                         // normalized min-sum
                         float mn1 = f_inf(), mn2 = f_inf();
                         float qf[kHold ? DCM : 1];
+                        float qh[L::kHoldLong ? DCM : 1];   // q of a long row (table form)
                         auto gather = [&](int k) {
                             // unused slots point at the group's +inf word
                             const float v = ldsf(ln.addr(p, k));
@@ -600,34 +616,56 @@ struct Decoder {
                             // go through the pairwise minimum (mn1 = mn2 = +inf
                             // before the first pair gives the first pair's
                             // order statistics)
-                            auto pair = [&](uint32_t w) {
-                                const float va = ldsf(ln.word_addr(w & 0xFFFFu));
-                                const float vb = ldsf(ln.word_addr(w >> 16));
+                            auto take = [&](float va, float vb) {
                                 S ^= __float_as_uint(va) ^ __float_as_uint(vb);
                                 const float lo = fminf(fabsf(va), fabsf(vb)), hi = fmaxf(fabsf(va), fabsf(vb));
                                 mn2 = fmin3(mn2, fmaxf(mn1, lo), hi);
                                 mn1 = fminf(mn1, lo);
                             };
+                            auto take1 = [&](float v) {
+                                S ^= __float_as_uint(v);
+                                const float av = fabsf(v);
+                                mn2 = fminf(mn2, fmaxf(mn1, av));
+                                mn1 = fminf(mn1, av);
+                            };
                             constexpr int kFull = DCM / kTabEdges, kTail = DCM % kTabEdges;
-#pragma unroll 1
-                            for (int c = 0; c < kFull; ++c) {
-                                const uint4 w = lds128(ln.tab + 16u * G * c);
-                                pair(w.x);
-                                pair(w.y);
-                                pair(w.z);
-                                pair(w.w);
-                            }
-                            if constexpr (kTail > 0) {
-                                const uint4 w = lds128(ln.tab + 16u * G * kFull);
-                                const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+                            if constexpr (L::kHoldLong) {
+                                // every chunk unrolled, the q of the row kept in qh
 #pragma unroll
-                                for (int h = 0; h < kTail / 2; ++h) pair(ww[h]);
-                                if constexpr (kTail & 1) {
-                                    const float v = ldsf(ln.word_addr(ww[kTail / 2] & 0xFFFFu));
-                                    S ^= __float_as_uint(v);
-                                    const float av = fabsf(v);
-                                    mn2 = fminf(mn2, fmaxf(mn1, av));
-                                    mn1 = fminf(mn1, av);
+                                for (int c = 0; c < L::kTabChunks; ++c) {
+                                    const uint4 w = lds128(ln.tab_entry(p, c));
+                                    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                    for (int h = 0; h < 4; ++h) {
+                                        const int k = c * kTabEdges + 2 * h;
+                                        if (k + 1 < DCM) {
+                                            qh[k] = ldsf(ln.word_addr(ww[h] & 0xFFFFu));
+                                            qh[k + 1] = ldsf(ln.word_addr(ww[h] >> 16));
+                                            take(qh[k], qh[k + 1]);
+                                        } else if (k < DCM) {
+                                            qh[k] = ldsf(ln.word_addr(ww[h] & 0xFFFFu));
+                                            take1(qh[k]);
+                                        }
+                                    }
+                                }
+                            } else {
+                                auto pair = [&](uint32_t w) {
+                                    take(ldsf(ln.word_addr(w & 0xFFFFu)), ldsf(ln.word_addr(w >> 16)));
+                                };
+#pragma unroll 1
+                                for (int c = 0; c < kFull; ++c) {
+                                    const uint4 w = lds128(ln.tab_entry(p, c));
+                                    pair(w.x);
+                                    pair(w.y);
+                                    pair(w.z);
+                                    pair(w.w);
+                                }
+                                if constexpr (kTail > 0) {
+                                    const uint4 w = lds128(ln.tab_entry(p, kFull));
+                                    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                    for (int h = 0; h < kTail / 2; ++h) pair(ww[h]);
+                                    if constexpr (kTail & 1) take1(ldsf(ln.word_addr(ww[kTail / 2] & 0xFFFFu)));
                                 }
                             }
                         } else {   // long rows: bounded unrolling keeps few loads in flight
@@ -657,33 +695,50 @@ struct Decoder {
 #pragma unroll
                                 for (int k = 0; k < DCM; ++k) put(k);
                             } else if constexpr (L::kTab) {
-                                // each q read again from its slot, then overwritten by r
-                                auto put_at = [&](uint32_t a) {
-                                    const float vk = ldsf(a);
+                                auto out_of = [&](float vk) {
                                     const bool is_min = fabsf(vk) == mn1;
-                                    const uint32_t out = (is_min ? m2 : m1) ^ (__float_as_uint(vk) & 0x80000000u);
+                                    return (is_min ? m2 : m1) ^ (__float_as_uint(vk) & 0x80000000u);
+                                };
+                                auto store = [&](uint32_t a, uint32_t out) {
                                     if (RC) sts32(a, out);
                                     else sts32_if(a, out, a != ln.inf_addr);
                                 };
-                                auto put2 = [&](uint32_t w) {
-                                    put_at(ln.word_addr(w & 0xFFFFu));
-                                    put_at(ln.word_addr(w >> 16));
-                                };
                                 constexpr int kFull = DCM / kTabEdges, kTail = DCM % kTabEdges;
-#pragma unroll 1
-                                for (int c = 0; c < kFull; ++c) {
-                                    const uint4 w = lds128(ln.tab + 16u * G * c);
-                                    put2(w.x);
-                                    put2(w.y);
-                                    put2(w.z);
-                                    put2(w.w);
-                                }
-                                if constexpr (kTail > 0) {
-                                    const uint4 w = lds128(ln.tab + 16u * G * kFull);
-                                    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+                                if constexpr (L::kHoldLong) {
+                                    // the held q decide each answer; the table gives the slots
 #pragma unroll
-                                    for (int h = 0; h < kTail / 2; ++h) put2(ww[h]);
-                                    if constexpr (kTail & 1) put_at(ln.word_addr(ww[kTail / 2] & 0xFFFFu));
+                                    for (int c = 0; c < L::kTabChunks; ++c) {
+                                        const uint4 w = lds128(ln.tab_entry(p, c));
+                                        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                        for (int h = 0; h < 4; ++h) {
+                                            const int k = c * kTabEdges + 2 * h;
+                                            if (k < DCM) store(ln.word_addr(ww[h] & 0xFFFFu), out_of(qh[k]));
+                                            if (k + 1 < DCM) store(ln.word_addr(ww[h] >> 16), out_of(qh[k + 1]));
+                                        }
+                                    }
+                                } else {
+                                    // each q read again from its slot, then overwritten by r
+                                    auto put_at = [&](uint32_t a) { store(a, out_of(ldsf(a))); };
+                                    auto put2 = [&](uint32_t w) {
+                                        put_at(ln.word_addr(w & 0xFFFFu));
+                                        put_at(ln.word_addr(w >> 16));
+                                    };
+#pragma unroll 1
+                                    for (int c = 0; c < kFull; ++c) {
+                                        const uint4 w = lds128(ln.tab_entry(p, c));
+                                        put2(w.x);
+                                        put2(w.y);
+                                        put2(w.z);
+                                        put2(w.w);
+                                    }
+                                    if constexpr (kTail > 0) {
+                                        const uint4 w = lds128(ln.tab_entry(p, kFull));
+                                        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                        for (int h = 0; h < kTail / 2; ++h) put2(ww[h]);
+                                        if constexpr (kTail & 1) put_at(ln.word_addr(ww[kTail / 2] & 0xFFFFu));
+                                    }
                                 }
                             } else {
 #pragma unroll 5
@@ -1075,14 +1130,18 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
 // Variant table: (id, G, check passes, row weight, variable passes, column
 // weight, minimum column weight, regular rows, check rule (0 min-sum,
 // 1 product-sum), block threads, min blocks per SM, slots per variable pass
-// (4 bits per pass, 0: the column weight in every pass), shared edge table).
+// (3 bits per pass, 0: the column weight in every pass), shared edge table).
 // Variants 13 and 14 take circuit-level detector models (rows of up to 35
 // edges, one shot per SM): 13 with 6 slots in every pass and the check-edge
 // indices read from global memory at each access, 14 with variables sorted by
 // degree into passes of 6, 5, 4, 3, ... slots (a third less shared memory)
 // and the check-edge indices in a shared-memory table.  Variant 15 is variant
 // 1 (HGP-like graphs) with passes of 4, 4, 4, 4, 3, ... slots: the degree-4
-// variables of a hypergraph product in the first passes.
+// variables of a hypergraph product in the first passes.  Variant 16 is the
+// circuit-level form with 512 threads per shot (two check passes, 18
+// variable passes of 6, 6, 5, 5, 4, 4, 3, ..., 3, 2 slots): at 128 registers
+// a thread keeps its row's 35 gathered q for the scatter instead of reading
+// them again.
 #define BPDC_VARIANTS(X)                                                  \
     X(0, 32, 3, 6, 5, 3, 3, true, 0, 256, 4, 0, false)                    \
     X(1, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0, false)                  \
@@ -1098,8 +1157,9 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
     X(11, 32, 4, 4, 4, 2, 1, false, 1, 256, 4, 0, false)                  \
     X(12, 32, 3, 6, 5, 3, 3, true, 1, 256, 4, 0, false)                   \
     X(13, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0, false)              \
-    X(14, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0x333333456ull, true)   \
-    X(15, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0x3333334444ull, false)
+    X(14, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0x36db72eull, true)       \
+    X(15, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0x1b6db924ull, false)        \
+    X(16, 512, 2, 35, 18, 6, 2, false, 0, 512, 1, 0x136db6db6e4b76ull, true)
 
 static const Variant kVariants[] = {
 #define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB) \

@@ -8,7 +8,11 @@ product-sum iterations with per-edge, per-iteration weights [2, T, E]
 ``ckpt_every`` iterations and recomputed per segment in the backward pass.
 
 ``train_weights`` fits the weights on shots the library samples itself, with
-the binary cross-entropy of the posteriors against the sampled errors.
+the binary cross-entropy of the posteriors against the sampled errors, or
+with ``coset_loss``: the soft probability that the residual of the last
+iteration's decision flips a logical operator (the right target on a
+degenerate code, where any correction in the error's coset succeeds) plus a
+soft syndrome-mismatch term.
 """
 from __future__ import annotations
 
@@ -47,6 +51,34 @@ def bce_loss(post, errors):
     return (e * torch.nn.functional.softplus(post) + (1 - e) * torch.nn.functional.softplus(-post)).mean()
 
 
+def odd_parity_probability(x, A):
+    """P(odd parity) of independent bits with probabilities x [B, N] over each
+    row of the 0/1 matrix A [R, N]: (1 - prod_j (1 - 2 x_j)) / 2, the product
+    taken in the log domain (magnitudes summed by a matmul, signs counted)."""
+    t = 1 - 2 * x
+    logabs = torch.log(t.abs().clamp_min(1e-30))
+    negatives = torch.remainder((t < 0).to(x.dtype) @ A.T, 2)
+    prod = torch.exp(logabs @ A.T) * (1 - 2 * negatives)
+    return (1 - prod) / 2
+
+
+def coset_loss(post, errors, syndromes, H, O, syndrome_weight: float = 1.0):
+    """An objective tied to the decoder's success on a degenerate code: on the
+    last iteration's posteriors (post [B, T, N]), with flip probabilities
+    p_j = sigma(-L_j), the residual e + e_hat has bit j odd with probability
+    q_j = e_j + p_j - 2 e_j p_j; the loss is the mean probability that the
+    residual flips a logical operator (rows of O: a correction in the right
+    coset scores 0 whatever its weight) plus syndrome_weight times the mean
+    probability that the hard decision misses a syndrome bit (rows of H).
+    errors [B, N] and syndromes [B, M] are float {0, 1}; H, O dense float."""
+    p = torch.sigmoid(-post[:, -1, :])
+    q = errors + p - 2 * errors * p
+    logical = odd_parity_probability(q, O).mean()
+    odd = odd_parity_probability(p, H)
+    miss = (syndromes * (1 - odd) + (1 - syndromes) * odd).mean()
+    return logical + syndrome_weight * miss
+
+
 def unpack_words(words, n: int):
     """int32 bit words [B, ceil(n/32)] -> float32 {0, 1} [B, n] on the same device."""
     w = words.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
@@ -55,18 +87,29 @@ def unpack_words(words, n: int):
 
 
 def train_weights(graph, T: int = 20, steps: int = 50, batch: int = 4096, lr: float = 0.01, seed: int = 11,
-                  clip: float = 20.0, ckpt_every: int = 5, weights=None):
-    """Adam on the BCE loss over freshly sampled batches (shot offsets advance
-    every step).  Returns (weights [2, T, E], list of losses)."""
+                  clip: float = 20.0, ckpt_every: int = 5, weights=None, objective: str = "bce", problem=None):
+    """Adam over freshly sampled batches (shot offsets advance every step) on
+    the mean BCE of every iteration's posteriors against the sampled errors
+    (objective "bce") or on coset_loss (objective "coset"; needs the problem
+    for its H and L).  Returns (weights [2, T, E], list of losses)."""
     dev = torch.device("cuda", graph.device)
     W = (torch.ones((2, T, graph.E), dtype=torch.float32, device=dev) if weights is None
          else weights.detach().clone()).requires_grad_(True)
     opt = torch.optim.Adam([W], lr=lr)
+    if objective == "coset":
+        H = torch.tensor(problem.H.toarray(), dtype=torch.float32, device=dev)
+        O = torch.tensor(problem.L.toarray(), dtype=torch.float32, device=dev)
+    elif objective != "bce":
+        raise ValueError(f"unknown objective {objective!r}")
     hist = []
     for s in range(steps):
         syn, _, err = graph.sample(batch, seed, s * batch, errors=True)
         post = weighted_bp(W, graph, syn, clip, ckpt_every)
-        loss = bce_loss(post, unpack_words(err, graph.N))
+        e = unpack_words(err, graph.N)
+        if objective == "bce":
+            loss = bce_loss(post, e)
+        else:
+            loss = coset_loss(post, e, unpack_words(syn, graph.M), H, O)
         opt.zero_grad()
         loss.backward()
         opt.step()
@@ -88,6 +131,17 @@ def logical_error_rate(graph, shots: int, seed: int, shot_offset: int = 0, chunk
         fails += int(cnt[1])
         done += n
     return fails / shots
+
+
+def binomial_interval(k: int, n: int, z: float = 1.96):
+    """Wilson score interval of a binomial proportion k / n."""
+    if n == 0:
+        return 0.0, 1.0
+    ph = k / n
+    den = 1 + z * z / n
+    c = (ph + z * z / (2 * n)) / den
+    h = z * (ph * (1 - ph) / n + z * z / (4 * n * n)) ** 0.5 / den
+    return c - h, c + h
 
 
 def select_weights(graph, weights, clip: float = 20.0, shots: int = 100000, seed: int = 99,
