@@ -108,18 +108,21 @@ def oracle_sample_plan(code: str) -> int:
     return 1600 if code == "hgp2500" else 16000
 
 
-def kernel_source_hash() -> str:
-    """SHA-256 (16 hex digits) of the device code and variant table of
-    bpdc_kernels.cu (everything before the host-side kVariants array), without
-    comments, blank lines and the checked build's guard blocks."""
+def kernel_source_hash(kernel_id: int) -> str:
+    """SHA-256 (16 hex digits) of what a kernel variant is built from: the device
+    code of bpdc_kernels.cu (everything before the variant table) and the
+    variant's own row of that table, without comments, blank lines and the
+    checked build's guard blocks.  Other variants' rows do not enter it."""
     import hashlib
     import re
     src = os.path.join(ROOT, "paper_2510_08695_gb300", "csrc", "bpdc_kernels.cu")
-    text = open(src, "rb").read()
-    code = text[:text.index(b"static const Variant kVariants[]")].decode()
-    code = re.sub(r"#ifdef BPDC_CHECKS\n.*?#endif\n", "", code, flags=re.S)
+    text = open(src).read()
+    cut = text.index("#define BPDC_VARIANTS")
+    code = re.sub(r"#ifdef BPDC_CHECKS\n.*?#endif\n", "", text[:cut], flags=re.S)
     code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", code, flags=re.S))
     code = "\n".join(line.rstrip() for line in code.splitlines() if line.strip())
+    row = re.search(r"X\(%d,[^)]*\)" % kernel_id, text[cut:])
+    code += "\n" + (re.sub(r"\s+", "", row.group(0)) if row else "")
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
@@ -131,7 +134,7 @@ def profiled_traffic(kernel_id: int, shots: int, edge_updates: int):
     (None, None, name) when no summary was taken from the current kernel
     source."""
     import glob
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(kernel_id)
     stale = None
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "decode_kernel_*.json"))):
         prof = json.load(open(path))
@@ -777,8 +780,9 @@ def extras(args, pkg, torch, batches, groups, stream, line, value, fails):
                   f"decode that uses them), weights 2 x {WBP_T} x {P6.E} (per edge, iteration and direction), "
                   f"Adam lr {WBP_LR}, {WBP_STEPS} batches of {WBP_BATCH} shots sampled at p=0.06, checkpoints "
                   "every 5 iterations; objectives: bce = mean BCE of every iteration's posteriors against the "
-                  "sampled errors; coset = probability that the last iteration's residual flips a logical operator "
-                  "plus the probability of a missed syndrome bit (a correction in the error's coset scores 0)",
+                  "sampled errors; coset = probability that each iteration's residual flips a logical operator "
+                  "plus the probability of a missed syndrome bit, averaged over the iterations (a correction in "
+                  "the error's coset scores 0)",
         "objectives": objectives, "held_out_shots": WBP_EVAL_SHOTS,
         "rule": "learned weights are used only where their BP+DC logical error rate is no worse than plain"}
 

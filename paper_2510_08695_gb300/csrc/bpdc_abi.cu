@@ -368,7 +368,7 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
     // automatic preference: one warp per shot for small graphs (3 blocks per
     // SM before 4: the same speed with fewer spills), then the 256- and
     // 512-thread groups
-    static const int kOrder[] = {7, 0, 12, 5, 11, 1, 15, 3, 2, 4, 6, 16, 14, 13};
+    static const int kOrder[] = {17, 7, 0, 12, 5, 11, 1, 15, 3, 2, 4, 6, 16, 14, 13, 18};
     Packed P{};
     int vid = -1;
     for (int id : kOrder) {

@@ -1141,7 +1141,8 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
 // circuit-level form with 512 threads per shot (two check passes, 18
 // variable passes of 6, 6, 5, 5, 4, 4, 3, ..., 3, 2 slots): at 128 registers
 // a thread keeps its row's 35 gathered q for the scatter instead of reading
-// them again.
+// them again.  Variants 17 and 18 have the shape of BB[[72,12,6]] (two check
+// and three variable passes of a warp: its fast path) at 4 and 6 blocks per SM.
 #define BPDC_VARIANTS(X)                                                  \
     X(0, 32, 3, 6, 5, 3, 3, true, 0, 256, 4, 0, false)                    \
     X(1, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0, false)                  \
@@ -1159,7 +1160,9 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
     X(13, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0, false)              \
     X(14, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0x36db72eull, true)       \
     X(15, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0x1b6db924ull, false)        \
-    X(16, 512, 2, 35, 18, 6, 2, false, 0, 512, 1, 0x136db6db6e4b76ull, true)
+    X(16, 512, 2, 35, 18, 6, 2, false, 0, 512, 1, 0x136db6db6e4b76ull, true)  \
+    X(17, 32, 2, 6, 3, 3, 3, true, 0, 256, 4, 0, false)                       \
+    X(18, 32, 2, 6, 3, 3, 3, true, 0, 256, 6, 0, false)
 
 static const Variant kVariants[] = {
 #define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB) \

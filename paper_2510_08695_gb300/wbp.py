@@ -9,7 +9,7 @@ product-sum iterations with per-edge, per-iteration weights [2, T, E]
 
 ``train_weights`` fits the weights on shots the library samples itself, with
 the binary cross-entropy of the posteriors against the sampled errors, or
-with ``coset_loss``: the soft probability that the residual of the last
+with ``coset_loss``: the soft probability that the residual of each
 iteration's decision flips a logical operator (the right target on a
 degenerate code, where any correction in the error's coset succeeds) plus a
 soft syndrome-mismatch term.
@@ -63,19 +63,23 @@ def odd_parity_probability(x, A):
 
 
 def coset_loss(post, errors, syndromes, H, O, syndrome_weight: float = 1.0):
-    """An objective tied to the decoder's success on a degenerate code: on the
-    last iteration's posteriors (post [B, T, N]), with flip probabilities
-    p_j = sigma(-L_j), the residual e + e_hat has bit j odd with probability
-    q_j = e_j + p_j - 2 e_j p_j; the loss is the mean probability that the
-    residual flips a logical operator (rows of O: a correction in the right
-    coset scores 0 whatever its weight) plus syndrome_weight times the mean
-    probability that the hard decision misses a syndrome bit (rows of H).
-    errors [B, N] and syndromes [B, M] are float {0, 1}; H, O dense float."""
-    p = torch.sigmoid(-post[:, -1, :])
-    q = errors + p - 2 * errors * p
+    """An objective tied to the decoder's success on a degenerate code, taken
+    at every unrolled iteration (post [B, T, N]) like the BCE objective: with
+    flip probabilities p_j = sigma(-L_j), the residual e + e_hat has bit j odd
+    with probability q_j = e_j + p_j - 2 e_j p_j; the loss is the mean
+    probability that the residual flips a logical operator (rows of O: a
+    correction in the right coset scores 0 whatever its weight) plus
+    syndrome_weight times the mean probability that the hard decision misses a
+    syndrome bit (rows of H).  errors [B, N] and syndromes [B, M] are float
+    {0, 1}; H, O dense float."""
+    B, T, N = post.shape
+    p = torch.sigmoid(-post).reshape(B * T, N)
+    e = errors[:, None, :].expand(B, T, N).reshape(B * T, N)
+    s = syndromes[:, None, :].expand(B, T, syndromes.shape[1]).reshape(B * T, -1)
+    q = e + p - 2 * e * p
     logical = odd_parity_probability(q, O).mean()
     odd = odd_parity_probability(p, H)
-    miss = (syndromes * (1 - odd) + (1 - syndromes) * odd).mean()
+    miss = (s * (1 - odd) + (1 - s) * odd).mean()
     return logical + syndrome_weight * miss
 
 

@@ -94,6 +94,37 @@ def test_adjoint_matches_finite_differences(setup):
         assert abs(fd - gg[idx]) <= 5e-2 * abs(gg[idx]) + 1e-3, (idx, fd, gg[idx])
 
 
+def test_coset_objective_gradient_matches_finite_differences(setup):
+    """The coset-aware objective (probability that each iteration's residual
+    flips a logical operator, plus missed syndrome bits) through the
+    hand-written adjoint against central differences (h = 1e-3) of the GPU
+    forward, at the weights with the largest gradients."""
+    pkg, wbp, P, g, e, s, T, W = setup
+    err = torch.tensor(e, dtype=torch.float64, device="cuda")
+    syn = torch.tensor(s, dtype=torch.float64, device="cuda")
+    H = torch.tensor(P.H.toarray(), dtype=torch.float64, device="cuda")
+    O = torch.tensor(P.L.toarray(), dtype=torch.float64, device="cuda")
+
+    scale = float(s.shape[0] * P.K)   # a sum over shots and observables, like the BCE check's
+
+    def loss(Wn):
+        return scale * float(wbp.coset_loss(_gpu_post(wbp, g, s, Wn).double(), err, syn, H, O))
+
+    Wg = torch.tensor(W, dtype=torch.float32, device="cuda", requires_grad=True)
+    post = wbp.weighted_bp(Wg, g, to_dev(s), 20.0, 3)
+    (scale * wbp.coset_loss(post.double(), err, syn, H, O)).backward()
+    gg = Wg.grad.double().cpu().numpy()
+    assert np.abs(gg).max() > 0
+    h = 1e-3
+    for k in np.argsort(-np.abs(gg).ravel())[:8]:
+        idx = np.unravel_index(k, gg.shape)
+        Wp, Wm = W.copy(), W.copy()
+        Wp[idx] += h
+        Wm[idx] -= h
+        fd = (loss(Wp) - loss(Wm)) / (2 * h)
+        assert abs(fd - gg[idx]) <= 5e-2 * abs(gg[idx]) + 1e-3, (idx, fd, gg[idx])
+
+
 def test_checkpoint_interval_does_not_change_results(setup):
     """Segments are recomputed with the forward's own arithmetic, so the
     posteriors and gradients are bit-identical for every interval k, and the

@@ -71,15 +71,16 @@ def test_coset_loss_gradient_finite_differences(dtype):
     e = torch.tensor((rng.uniform(size=(2, P.N)) < 0.05).astype(np.float64), dtype=dtype)
     s = torch.remainder(e @ H.T, 2)
     post = torch.tensor(rng.normal(2.0, 2.0, size=(2, 3, P.N)), dtype=torch.float64, requires_grad=True)
+    # every iteration enters the loss: perturb the middle and the last one
     loss = wbp.coset_loss(post, e.double(), s.double(), H.double(), O.double())
     loss.backward()
     g = post.grad.numpy()
     h = 1e-6
-    for (b, j) in [(0, 0), (1, 5), (0, 40)]:
+    for (b, t, j) in [(0, 2, 0), (1, 1, 5), (0, 2, 40), (1, 0, 7)]:
         p1 = post.detach().clone()
-        p1[b, -1, j] += h
+        p1[b, t, j] += h
         p2 = post.detach().clone()
-        p2[b, -1, j] -= h
+        p2[b, t, j] -= h
         fd = (wbp.coset_loss(p1, e.double(), s.double(), H.double(), O.double())
               - wbp.coset_loss(p2, e.double(), s.double(), H.double(), O.double())).item() / (2 * h)
-        assert abs(fd - g[b, -1, j]) < 1e-6 * max(1.0, abs(fd))
+        assert abs(fd - g[b, t, j]) < 1e-6 * max(1.0, abs(fd))
