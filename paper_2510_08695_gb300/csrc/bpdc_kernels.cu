@@ -189,15 +189,19 @@ __device__ __forceinline__ float phi(float x) { return log1pf(2.0f / expm1f(x));
 // phi(sum_j phi(x_j)) = -log sum_j e^-x_j + O(e^-2m), which lowers by exactly s.
 constexpr float kPhiShift = 20.0f;
 
-// A check's minimum |q| as it enters the outgoing message: at most the cap,
-// and 0 below the smallest normal float.  The hard-decision tag turns a
-// message that is exactly 0 into the smallest denormal when its sender's
-// decision is 1; without the flush that denormal would move an exact 0 of the
-// rule (and with it a posterior L = 0, whose decision is 1) off zero.  No
+// A check's minimum |q| as it enters the outgoing message, scaled by a (the
+// min-sum scale, or 1): at most the cap, and 0 below the smallest normal
+// float.  The hard-decision tag turns a message that is exactly 0 into the
+// smallest denormal when its sender's decision is 1; without the flush that
+// denormal would move an exact 0 of the rule (and with it a posterior L = 0,
+// whose decision is 1) off zero.  The multiply flushes a denormal operand (and
+// result) to zero itself (.ftz), so the flush costs no instruction; no
 // message of the rule is nonzero and that small otherwise.
-__device__ __forceinline__ float clamp_min(float m)
+__device__ __forceinline__ float scaled_min(float a, float m)
 {
-    return m < 1.17549435e-38f ? 0.0f : fminf(m, kLlrCap);
+    float r;
+    asm("mul.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(fminf(m, kLlrCap)));
+    return r;
 }
 
 // Shared words at the start of every group's region: 0-1 shot broadcast
@@ -573,7 +577,9 @@ struct Decoder {
                     constexpr bool kHold = DCM <= 16;
                     static_assert(kHold || RULE == 0, "product-sum rows are limited to 16 edges");
                     uint32_t qb[kHold ? DCM : 1];
-                    uint32_t S = ((sbits >> p) & 1u) ? 0x80000001u : 0u;
+                    // the syndrome bit enters as sign and parity: 0 or 0x80000001
+                    // (a multiply, which the FMA pipe takes off the busy ALU pipe)
+                    uint32_t S = ((sbits >> p) & 1u) * 0x80000001u;
                     if constexpr (RULE == 0) {
                         // normalized min-sum
                         float mn1 = f_inf(), mn2 = f_inf();
@@ -677,9 +683,10 @@ struct Decoder {
                             // the minimum over the other edges is min2 for the edge
                             // holding min1 and min1 for all others; with a tie at
                             // min1 both are equal, so no argmin is needed
-                            const uint32_t Sm = S & 0x80000000u;
-                            uint32_t m1 = __float_as_uint(alpha * clamp_min(mn1)) ^ Sm;
-                            uint32_t m2 = __float_as_uint(alpha * clamp_min(mn2)) ^ Sm;
+                            // the row's sign parity rides on the scale factor
+                            const float sa = __uint_as_float(__float_as_uint(alpha) ^ (S & 0x80000000u));
+                            uint32_t m1 = __float_as_uint(scaled_min(sa, mn1));
+                            uint32_t m2 = __float_as_uint(scaled_min(sa, mn2));
                             if (RC && !live) m1 = m2 = 0x7F800000u;   // idle check: writes +inf back
                             auto put = [&](int k) {
                                 const uint32_t a = ln.addr(p, k);
@@ -796,7 +803,7 @@ struct Decoder {
                                 const uint32_t a = ln.addr(p, k);
                                 const bool is_min = fabsf(__uint_as_float(qb[k])) == mn1;
                                 const bool own_b = sb != sa && is_min;
-                                float mag = pair ? clamp_min(is_min ? mn2 : mn1)
+                                float mag = pair ? scaled_min(1.0f, is_min ? mn2 : mn1)
                                                  : (own_b ? rb : sa + phi(pre + suf[k + 1]));
                                 mag = fminf(mag, kLlrCap);
                                 pre += f[k];

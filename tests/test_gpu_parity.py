@@ -11,6 +11,8 @@ own outcome changes under rounding-sized prior perturbations; at least
 case states the measured reason); failure counts within two binomial sigma;
 every posterior entry within 1e-4 relative or, where the oracle amplifies
 rounding beyond that, within twice the oracle's own spread."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -279,13 +281,20 @@ def test_plain_and_persistent_identical_and_offsets(pkg):
         assert (a[k] == torch.cat([c1[k], c2[k]])).all(), k
 
 
-@pytest.mark.parametrize("name", ["bb144", "hgp", "phen"])
-def test_layouts_give_identical_results(pkg, name):
-    """The bank-conflict-aware layout changes no arithmetic: bit-identical outputs."""
+@pytest.mark.parametrize("name,kernel", [("bb144", None), ("hgp", None), ("phen", None), ("hgp", 15),
+                                         ("circuit", 16)])
+def test_layouts_give_identical_results(pkg, name, kernel):
+    """The bank-conflict-aware layout changes no arithmetic: bit-identical
+    outputs; also for the slot-profile variants, whose identity placement
+    sorts variables by degree into the passes."""
+    from bpdc_inputs import circuit
     P = {"bb144": lambda: bi.bb_problem("bb144", 0.07), "hgp": lambda: bi.hgp_problem(0.06),
-         "phen": lambda: bi.phenomenological_bb_problem("bb144", 12, 0.008)}[name]()
+         "phen": lambda: bi.phenomenological_bb_problem("bb144", 12, 0.008),
+         "circuit": lambda: circuit.circuit_level_problem("bb72", 6, 2e-3)}[name]()
     _, s, o = sample_shots(P, SEED + 21, 0, 1500 if P.N < 1000 else 400)
-    g = pkg.Graph.from_problem(P)
+    g = pkg.Graph.from_problem(P, pkg.Options(max_iter=200) if name == "circuit" else None)
+    if kernel is not None:
+        g.set_kernel(kernel)
     outs = []
     for mode in (1, 0):
         g.set_layout(mode)
@@ -392,6 +401,27 @@ def test_edge_cases(pkg, oracle_mod, torch_cuda):
     st = rs["status"].cpu().numpy()
     e = from_dev(rs["corrections"], P.N)
     assert (syndromes(e[st < 2], P.H) == s2[st < 2]).all()
+
+
+def test_shot_limit_per_launch(pkg, torch_cuda):
+    """One launch takes at most 2^32 - 2^24 shots (groups wider than a warp
+    pass their work tickets through a 32-bit shared word): a larger call is
+    refused with UNSUPPORTED before anything is launched or read (the buffers
+    here hold one shot), and the library stays usable."""
+    torch = torch_cuda
+    from paper_2510_08695_gb300 import _bpdc
+    P = bi.bb_problem("bb72", 0.05)
+    g = pkg.Graph.from_problem(P)
+    syn = torch.zeros((1, g.MW), dtype=torch.int32, device="cuda")
+    out = g.alloc_outputs(1)
+    o = g._outputs(out)
+    big = (1 << 32) - (1 << 24) + 1
+    rc = _bpdc._lib.bpdc_decode(g.handle, big, syn.data_ptr(), 0, ctypes.byref(o), 1, None)
+    assert rc == _bpdc.ERR_UNSUPPORTED
+    assert b"shots per launch" in _bpdc._lib.bpdc_last_error()
+    ok = g.decode(syn, 0)
+    torch.cuda.synchronize()
+    assert int(ok["status"][0]) == 0
 
 
 def test_smem_peak_microbenchmark(pkg):
