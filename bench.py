@@ -197,8 +197,10 @@ def phenomenological_leg(args, pkg, torch, stream, peak_gbs) -> dict:
         items.append(dict(graph=g, syndromes=syn, obs_true=obs, shot_offset=0, out=g.alloc_outputs(spp),
                           counters=torch.zeros(4, dtype=torch.int64, device="cuda"), p=p))
     torch.cuda.synchronize()
+    # the probe: 10^5 shots of the p = 0.010 point, enough that the few shots
+    # running all 1000 + 1000 iterations do not decide the launch's length alone
     probe = items[-1]
-    tune = autotune(probe["graph"], probe["syndromes"][:min(20000, spp)].contiguous(), 0)
+    tune = autotune(probe["graph"], probe["syndromes"][:min(100000, spp)].contiguous(), 0)
     for it in items:
         it["graph"].set_kernel(tune["best"])
     vid = tune["best"]

@@ -166,6 +166,19 @@ int bpdc_graph_set_layout(bpdc_graph_t g, int32_t mode);
  * the identity placement and the CSR order. */
 int bpdc_layout_plan(const bpdc_csr *H, int32_t G, int32_t optimize, int32_t *pos_of_var, int32_t *edge_round);
 
+/* The same planner under a slot profile (host only; the layouts of the kernel
+ * variants whose variable passes have different slot counts):
+ * pass_slots[n_pass] (non-increasing, >= 1; n_pass >= ceil(N/G)) gives the
+ * message slots of every variable in pass p (positions [p*G, (p+1)*G)); the
+ * variables are placed so that each one's column weight is at most its pass's
+ * slot count (per bank class, the number of variables of weight >= d stays
+ * within the positions of passes with >= d slots; each bank's members fill its
+ * positions in order of decreasing weight).  n_pass = 0: no profile (as
+ * bpdc_layout_plan).  INVALID_ARG for a malformed profile; UNSUPPORTED when the
+ * column weights cannot fit it. */
+int bpdc_layout_plan_slots(const bpdc_csr *H, int32_t G, int32_t optimize, int32_t n_pass,
+                           const int32_t *pass_slots, int32_t *pos_of_var, int32_t *edge_round);
+
 /* Outputs of a decode call (device pointers; NULL where optional). */
 typedef struct {
     uint32_t *corrections;       /* required: [B][ceil(N/32)] e_hat bits (cut variables 0) */

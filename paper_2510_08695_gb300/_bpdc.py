@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
         "bpdc_kernel_count": (ctypes.c_int, []),
         "bpdc_graph_set_layout": (ctypes.c_int, [vp, i32]),
         "bpdc_layout_plan": (ctypes.c_int, [ctypes.POINTER(_Csr), i32, i32, _i32p, _i32p]),
+        "bpdc_layout_plan_slots": (ctypes.c_int, [ctypes.POINTER(_Csr), i32, i32, i32, _i32p, _i32p, _i32p]),
         "bpdc_decode": (ctypes.c_int, [vp, i64, vp, u64, ctypes.POINTER(_Outputs), ctypes.c_int, vp]),
         "bpdc_decode_multi": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
         "bpdc_decode_multi_noalloc": (ctypes.c_int, [ctypes.POINTER(_Batch), i32, vp]),
@@ -430,14 +431,22 @@ def decode_backward(graph: Graph, syndromes, weights, T: int, clip: float, ckpt_
     return grad_weights
 
 
-def layout_plan(H, G: int, optimize: bool = True):
-    """Host-only layout planner: (pos_of_var [N], edge_round [nnz] in H's CSR order)."""
+def layout_plan(H, G: int, optimize: bool = True, pass_slots=None):
+    """Host-only layout planner: (pos_of_var [N], edge_round [nnz] in H's CSR
+    order); ``pass_slots`` (message slots of each variable pass) places the
+    variables under a slot profile (bpdc_layout_plan_slots)."""
     lib = load()
     h, keep = _csr(H)
     pos = np.zeros(h.cols, np.int32)
     rnd = np.zeros(max(int(h.nnz), 1), np.int32)
-    _check(lib.bpdc_layout_plan(ctypes.byref(h), int(G), int(bool(optimize)), pos.ctypes.data_as(_i32p),
-                                rnd.ctypes.data_as(_i32p)))
+    if pass_slots is None:
+        _check(lib.bpdc_layout_plan(ctypes.byref(h), int(G), int(bool(optimize)), pos.ctypes.data_as(_i32p),
+                                    rnd.ctypes.data_as(_i32p)))
+    else:
+        ps = np.ascontiguousarray(pass_slots, dtype=np.int32)
+        _check(lib.bpdc_layout_plan_slots(ctypes.byref(h), int(G), int(bool(optimize)), int(ps.size),
+                                          ps.ctypes.data_as(_i32p), pos.ctypes.data_as(_i32p),
+                                          rnd.ctypes.data_as(_i32p)))
     return pos, rnd[:int(h.nnz)]
 
 

@@ -728,18 +728,38 @@ int bpdc_graph_set_plan(bpdc_graph_t g, int32_t threads_per_shot)
 
 int bpdc_kernel_count(void) { return num_variants(); }
 
-int bpdc_layout_plan(const bpdc_csr *H, int32_t G, int32_t optimize, int32_t *pos_of_var, int32_t *edge_round)
+int bpdc_layout_plan_slots(const bpdc_csr *H, int32_t G, int32_t optimize, int32_t n_pass, const int32_t *pass_slots,
+                           int32_t *pos_of_var, int32_t *edge_round)
 {
     HostCsr h;
     int rc = copy_csr(H, "H", h);
     if (rc != BPDC_OK) return rc;
     if (G < 32 || G % 32 != 0 || G > 1024) return fail(BPDC_ERR_INVALID_ARG, "G must be a multiple of 32 in [32, 1024]");
     if (!pos_of_var || !edge_round) return fail(BPDC_ERR_INVALID_ARG, "NULL output");
+    const int pv = std::max(1, (h.cols + G - 1) / G);
+    std::vector<int> pass_cv;
+    std::vector<int> deg(h.cols, 0);
+    for (int32_t c : h.col) deg[c]++;
+    if (n_pass > 0) {
+        if (!pass_slots) return fail(BPDC_ERR_INVALID_ARG, "pass_slots is NULL");
+        if (n_pass < pv) return fail(BPDC_ERR_INVALID_ARG, "%d passes cannot hold %d variables at G = %d", n_pass, h.cols, G);
+        for (int p = 0; p < pv; ++p) {
+            if (pass_slots[p] < 1 || (p > 0 && pass_slots[p] > pass_slots[p - 1]))
+                return fail(BPDC_ERR_INVALID_ARG, "pass_slots must be positive and non-increasing");
+            pass_cv.push_back(pass_slots[p]);
+        }
+        std::vector<int> ds(deg);
+        std::sort(ds.begin(), ds.end(), std::greater<int>());
+        for (int j = 0; j < h.cols; ++j)
+            if (ds[j] > pass_cv[j / G]) return fail(BPDC_ERR_UNSUPPORTED, "the column weights do not fit the passes");
+    }
     int dc = 1;
     for (int i = 0; i < h.rows; ++i) dc = std::max(dc, h.ptr[i + 1] - h.ptr[i]);
-    const int npos = std::max(1, (h.cols + G - 1) / G) * G;
     Layout lay;
-    plan_layout(h.rows, h.cols, h.ptr, h.col, G, npos, dc, optimize != 0, std::vector<int>(), lay);
+    plan_layout(h.rows, h.cols, h.ptr, h.col, G, pv * G, dc, optimize != 0, pass_cv, lay);
+    for (int j = 0; j < h.cols && !pass_cv.empty(); ++j)
+        if (deg[j] > pass_cv[lay.pos_of_var[j] / G])
+            return fail(BPDC_ERR_UNSUPPORTED, "the planner could not place column %d within its pass width", j);
     std::copy(lay.pos_of_var.begin(), lay.pos_of_var.end(), pos_of_var);
     // edge_round is reported in the caller's CSR order (copy_csr sorted each row)
     for (int i = 0; i < h.rows; ++i)
@@ -749,6 +769,11 @@ int bpdc_layout_plan(const bpdc_csr *H, int32_t G, int32_t optimize, int32_t *po
             edge_round[a] = lay.edge_round[b];
         }
     return BPDC_OK;
+}
+
+int bpdc_layout_plan(const bpdc_csr *H, int32_t G, int32_t optimize, int32_t *pos_of_var, int32_t *edge_round)
+{
+    return bpdc_layout_plan_slots(H, G, optimize, 0, nullptr, pos_of_var, edge_round);
 }
 
 int bpdc_graph_set_layout(bpdc_graph_t g, int32_t mode)

@@ -293,6 +293,7 @@ struct Lane {
     // when a thread has the registers for it (512 threads or fewer per SM);
     // else the scatter reads each q again
     static constexpr bool kHoldLong = kTab && G <= 512;
+    static_assert(!kHoldLong || kTab, "held long rows need the shared edge table");
 
     __device__ __forceinline__ uint32_t tab_entry(int p, int c) const
     {
@@ -864,7 +865,13 @@ struct Decoder {
                     if (u == 0) x = atomicAdd((unsigned long long *)ld.work, 1ull);
                     x = __shfl_sync(grp.mask, x, grp.leader);
                 } else {
-                    uint32_t *misc = region + 0;  // two words, double buffered
+                    // the ticket goes through a shared word (two, alternating);
+                    // drawn only when the group is free, so that a shot never
+                    // waits behind a long one on a busy group.  This barrier
+                    // also keeps a fast lane from writing the next shot's slots
+                    // or staging (of another graph, perhaps) before every lane
+                    // has copied out the previous shot
+                    uint32_t *misc = region + 0;
                     if (u == 0) misc[bufsel] = (uint32_t)atomicAdd((unsigned long long *)ld.work, 1ull);
                     grp.sync();
                     x = misc[bufsel];
@@ -917,8 +924,6 @@ struct Decoder {
                 const int i = p * G + u;
                 if (p < g.pc && i < g.M) sbits |= ((__ldg(sy + (i >> 5)) >> (i & 31)) & 1u) << p;
             }
-            const bool nonzero = grp.any(sbits != 0);
-
             uint32_t hd = 0;
             int st = 0, it1 = 0, it2 = 0;
             bool ran_dc = false;
@@ -935,20 +940,23 @@ struct Decoder {
                     }
                 }
             }
+            // initial messages of the first run (also writes the prior as the
+            // posterior when one is requested), and the correction and
+            // logical-flip staging cleared (each lane the words it copies out
+            // in the epilogue); the vote is the barrier that publishes both
+            hd = init(g, ln, u, post_row);
+            for (int x = u; x < g.NW; x += G) cm[x] = 0;
+            for (int x = u; x < g.KW; x += G) ls[x] = 0;
+            const bool nonzero = grp.any(sbits != 0);
             if (!cut_in && !nonzero && g.zero_ok) {
-                // converged before the first iteration: e_hat = 0
-                if (post_row) {
-#pragma unroll
-                    for (int p = 0; p < PVM; ++p)
-#ifdef BPDC_CHECKS
-                        if (p < g.pv && ((ln.vvalid >> p) & 1u) && !post_ok(g, (long long)p * G + u)) {} else
-#endif
-                        if (p < g.pv && ((ln.vvalid >> p) & 1u)) post_row[__ldg(g.pos_col + p * G + u)] = ln.lamv[p];
-                }
+                // converged before the first iteration: e_hat = 0 (every prior < 1/2)
+                hd = 0;
             } else {
                 for (bool second = false;; second = true) {
-                    hd = init(g, ln, u, post_row);
-                    grp.sync();
+                    if (second) {
+                        hd = init(g, ln, u, post_row);
+                        grp.sync();
+                    }
                     int iters = 0;
                     const bool ok = (g.pc == PCM && g.pv == PVM && !post_row)
                                         ? run<true>(g, ln, grp, sbits, hd, iters, post_row)
@@ -986,49 +994,56 @@ struct Decoder {
                     }
                     lam_dirty = true;
                     grp.sync();
+                    // the staging again (it held the cut mask), published by the
+                    // barrier after the second run's initial messages
+                    for (int x = u; x < g.cmw; x += G) cm[x] = 0;
                     // ---- a8: BP again on the cut graph ----
                 }
             }
 
             // ---- a9: epilogue ----
+            // corrections and logical flips from the set decision bits into the
+            // cleared staging (shared atomics), published by one barrier
             uint32_t *corr = bd.corr + (size_t)b * g.NW;
-            bool fail_local = false;
-            const bool any_set = grp.any(hd != 0);
-            if (!any_set) {
-                for (int x = u; x < g.NW; x += G) corr[x] = 0;
-                for (int x = u; x < g.KW; x += G) {
-                    if (bd.lflips) bd.lflips[(size_t)b * g.KW + x] = 0;
-                    if (bd.obs_true && __ldg(bd.obs_true + (size_t)b * g.KW + x) != 0) fail_local = true;
-                }
-            } else {
-                for (int x = u; x < g.NW; x += G) cm[x] = 0;
-                for (int x = u; x < g.KW; x += G) ls[x] = 0;
-                grp.sync();
 #pragma unroll
-                for (int p = 0; p < PVM; ++p) {
-                    if ((hd >> p) & 1u) {
-                        const int j = p * G + u;
-                        const int c = __ldg(g.pos_col + j);
+            for (int p = 0; p < PVM; ++p) {
+                if ((hd >> p) & 1u) {
+                    const int j = p * G + u;
+                    const int c = __ldg(g.pos_col + j);
 #ifdef BPDC_CHECKS
-                        if (!check_index(7, c, g.N)) continue;
+                    if (!check_index(7, c, g.N)) continue;
 #endif
-                        atomicOr(cm + (c >> 5), 1u << (c & 31));
-                        const uint32_t *lc = g.l_bits + (size_t)j * g.KW;
-                        for (int x = 0; x < g.KW; ++x) {
-                            const uint32_t v = __ldg(lc + x);
-                            if (v) atomicXor(ls + x, v);
-                        }
+                    atomicOr(cm + (c >> 5), 1u << (c & 31));
+                    const uint32_t *lc = g.l_bits + (size_t)j * g.KW;
+                    for (int x = 0; x < g.KW; ++x) {
+                        const uint32_t v = __ldg(lc + x);
+                        if (v) atomicXor(ls + x, v);
                     }
                 }
-                grp.sync();
-                for (int x = u; x < g.NW; x += G) corr[x] = cm[x];
-                for (int x = u; x < g.KW; x += G) {
-                    const uint32_t v = ls[x];
-                    if (bd.lflips) bd.lflips[(size_t)b * g.KW + x] = v;
-                    if (bd.obs_true && __ldg(bd.obs_true + (size_t)b * g.KW + x) != v) fail_local = true;
-                }
             }
-            const bool fail = grp.any(fail_local) || st == 2;
+            grp.sync();
+            bool fail_local = false;
+            for (int x = u; x < g.NW; x += G) corr[x] = cm[x];
+            for (int x = u; x < g.KW; x += G) {
+                const uint32_t v = ls[x];
+                if (bd.lflips) bd.lflips[(size_t)b * g.KW + x] = v;
+                if (bd.obs_true && __ldg(bd.obs_true + (size_t)b * g.KW + x) != v) fail_local = true;
+            }
+            // a logical flip differing from the true one: the lanes holding
+            // logical words are the group's first warp when there are at most
+            // 32 of them, so a warp vote suffices there
+            bool fail_obs;
+            if constexpr (G > 32) {
+                if (g.KW <= 32) {
+                    const bool v = u < 32 ? __any_sync(0xFFFFFFFFu, fail_local) != 0 : false;
+                    fail_obs = v;
+                } else {
+                    fail_obs = grp.any(fail_local);
+                }
+            } else {
+                fail_obs = grp.any(fail_local);
+            }
+            const bool fail = fail_obs || st == 2;
             if (u == 0) {
                 bd.status[b] = (uint8_t)st;
                 if (bd.iters) bd.iters[b] = (uint32_t)it1 | ((uint32_t)it2 << 16);

@@ -48,3 +48,42 @@ def test_layout_is_valid_and_cuts_conflicts(name, G):
     # within 10 % of one wavefront per round (HGP-2500, whose groups need
     # exactly 7 edges in every bank, keeps an overflow of about 18 edges)
     assert w_opt < 0.6 * w_nat and w_opt <= 1.1 * ideal, (w_opt, w_nat, ideal)
+
+
+@pytest.mark.parametrize("name,G,slots", [
+    ("circuit", 1024, [6, 5, 4, 3, 3, 3, 3, 3, 3]),
+    ("circuit", 512, [6, 6, 5, 5, 4, 4] + [3] * 11 + [2]),
+    ("hgp", 256, [4, 4, 4, 4, 3, 3, 3, 3, 3, 3]),
+])
+def test_slot_profile_layout(name, G, slots):
+    """Under a slot profile every variable sits in a pass with at least as many
+    slots as its column weight, and the check update's modelled wavefronts
+    stay within 10 % of one per round (the profiles of the circuit-level and
+    HGP kernel variants)."""
+    if name == "circuit":
+        from bpdc_inputs import circuit
+        P = circuit.circuit_level_problem("bb144", 12, 1e-3)
+    else:
+        P = bi.hgp_problem(0.05)
+    H = P.H.tocsr()
+    deg = np.diff(H.tocsc().indptr)
+    pos, rnd = _bpdc.layout_plan(H, G, True, pass_slots=slots)
+    assert len(set(pos.tolist())) == H.shape[1] and pos.min() >= 0 and pos.max() < len(slots) * G
+    assert (deg <= np.asarray(slots)[pos // G]).all()
+    w_opt, ideal = wavefronts(H, pos, rnd)
+    assert w_opt <= 1.1 * ideal, (w_opt, ideal)
+    # the identity placement under the profile sorts by decreasing weight
+    pos0, _ = _bpdc.layout_plan(H, G, False, pass_slots=slots)
+    assert (deg <= np.asarray(slots)[pos0 // G]).all()
+    assert (np.diff(deg[np.argsort(pos0)]) <= 0).all()
+
+
+def test_slot_profile_rejections():
+    P = bi.hgp_problem(0.05)
+    H = P.H.tocsr()
+    with pytest.raises(_bpdc.BpdcError):   # increasing profile
+        _bpdc.layout_plan(H, 256, True, pass_slots=[3] * 5 + [4] * 5)
+    with pytest.raises(_bpdc.BpdcError):   # too few slots for the 900 degree-4 columns
+        _bpdc.layout_plan(H, 256, True, pass_slots=[4, 4, 4] + [3] * 7)
+    with pytest.raises(_bpdc.BpdcError):   # too few passes
+        _bpdc.layout_plan(H, 256, True, pass_slots=[4] * 5)
