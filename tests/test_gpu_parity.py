@@ -304,14 +304,15 @@ def test_layouts_give_identical_results(pkg, name, kernel):
         assert (a == b).all() or (k == "posterior_llr" and bool(((a == b) | (a.isnan() & b.isnan())).all())), k
 
 
-@pytest.mark.parametrize("name", ["bb72", "bb144", "hgp"])
+@pytest.mark.parametrize("name", ["bb72", "bb144", "hgp", "phen"])
 def test_every_variant_gives_identical_results(pkg, name):
     """Every compiled kernel variant that accepts a graph (as the autotuner
     tries them, including the circuit-level one on small codes) decodes it
     bit-identically: min-sum takes order-free minima, and each variable sums
     its edges in ascending check order whatever the variant."""
     P = {"bb72": lambda: bi.bb_problem("bb72", 0.06), "bb144": lambda: bi.bb_problem("bb144", 0.07),
-         "hgp": lambda: bi.hgp_problem(0.06)}[name]()
+         "hgp": lambda: bi.hgp_problem(0.06),
+         "phen": lambda: bi.phenomenological_bb_problem("bb144", 12, 0.01)}[name]()
     _, s, o = sample_shots(P, SEED + 22, 0, 1200 if P.N < 1000 else 300)
     g = pkg.Graph.from_problem(P)
     ks = g.kernels()
