@@ -367,8 +367,9 @@ int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
 {
     // automatic preference: one warp per shot for small graphs (3 blocks per
     // SM before 4: the same speed with fewer spills), then the 256- and
-    // 512-thread groups
-    static const int kOrder[] = {17, 7, 0, 12, 5, 11, 1, 15, 3, 2, 4, 6, 16, 14, 13, 18};
+    // 512-thread groups (a slot-profile variant before the uniform one of the
+    // same shape: it is faster wherever its profile fits the graph)
+    static const int kOrder[] = {17, 7, 0, 12, 5, 11, 15, 1, 3, 2, 4, 6, 16, 14, 13, 18};
     Packed P{};
     int vid = -1;
     for (int id : kOrder) {
