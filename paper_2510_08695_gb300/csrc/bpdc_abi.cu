@@ -211,6 +211,9 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
     if (P.pc > v.pc_max || P.pv > v.pv_max || dmax > v.dc_max || cmax > v.cv_max) return false;
     if (v.regular_rows && (dmin != v.dc_max || dmax != v.dc_max)) return false;
     if (cmin < v.cv_min) return false;
+    // a shared last check pass (regular rows only) holds G / tail checks
+    const bool tail = v.tail > 0 && P.pc == v.pc_max;
+    if (v.tail > 0 && (!v.regular_rows || (tail && M - (P.pc - 1) * G > G / v.tail))) return false;
     P.dc = std::max(dmax, 1);
     P.cv = v.cv_max;
     // slots per pass (the variant's profile), and the degrees it can hold
@@ -277,10 +280,16 @@ bool pack(const bpdc_graph_s &g, const Variant &v, Packed &P)
             for (size_t a = 0; a < E; ++a) P.wts[(size_t)h * P.slots + edge_slot[a]] = g.w_host[h * E + a];
     }
     P.chk_idx.assign((size_t)P.pc * P.dc * G, kNoEdge);
+    const int tail_e = v.tail > 0 ? (v.dc_max + v.tail - 1) / v.tail : 0;   // edges per lane in it
     for (int i = 0; i < M; ++i) {
         const int p = i / G, u = i % G;
-        for (int a = g.H.ptr[i]; a < g.H.ptr[i + 1]; ++a)
-            P.chk_idx[((size_t)p * P.dc + lay.edge_round[a]) * G + u] = (uint16_t)edge_slot[a];
+        for (int a = g.H.ptr[i]; a < g.H.ptr[i + 1]; ++a) {
+            const int r = lay.edge_round[a];
+            if (tail && p == P.pc - 1)   // edge r of the pass's u-th check: lane u*tail + r/E, entry r%E
+                P.chk_idx[((size_t)p * P.dc + r % tail_e) * G + u * v.tail + r / tail_e] = (uint16_t)edge_slot[a];
+            else
+                P.chk_idx[((size_t)p * P.dc + r) * G + u] = (uint16_t)edge_slot[a];
+        }
     }
     // the same edges as word indices of the group's region (12 misc words
     // first; 2 = the +inf word), with the variant's full row width per pass
@@ -366,10 +375,11 @@ size_t put(std::vector<char> &blob, const std::vector<T> &v)
 int plan_and_upload(bpdc_graph_s *g, int want_G, int want_id = -1)
 {
     // automatic preference: one warp per shot for small graphs (3 blocks per
-    // SM before 4: the same speed with fewer spills), then the 256- and
-    // 512-thread groups (a slot-profile variant before the uniform one of the
-    // same shape: it is faster wherever its profile fits the graph)
-    static const int kOrder[] = {17, 7, 0, 12, 5, 11, 15, 1, 3, 2, 4, 6, 16, 14, 13, 18};
+    // SM before 4: the same speed with fewer spills; a shared last check pass
+    // before the plain form of the same shape), then the 256- and 512-thread
+    // groups (a slot-profile variant before the uniform one of the same shape:
+    // it is faster wherever its profile fits the graph)
+    static const int kOrder[] = {19, 17, 20, 7, 0, 12, 5, 11, 15, 1, 3, 2, 4, 6, 16, 14, 13, 18};
     Packed P{};
     int vid = -1;
     for (int id : kOrder) {

@@ -40,7 +40,10 @@ constexpr int kTabEdges = 8;
 
 // Device-resident decoding problem, laid out for a group of G threads per
 // shot.  Variable j sits at lane j % G, pass j / G; check i at lane i % G,
-// pass i / G.  Each variable owns `cv` consecutive message slots per pass:
+// pass i / G, except in a shared last check pass (Variant::tail = S lanes per
+// check): its c-th check sits on lanes c*S .. c*S+S-1, lane c*S+s holding the
+// check's edges s*E .. s*E+E-1 (E = ceil(dc_max / S)) as its entries
+// 0 .. E-1 of chk_idx.  Each variable owns `cv` consecutive message slots per pass:
 // slot(p, m, u) = (p * cv + m) * G + u holds the message of its m-th edge
 // (edges of a variable in ascending check order); unused slots hold 0.
 struct DevGraph {
@@ -132,6 +135,7 @@ struct Variant {
     int min_blocks;      // launch bound: resident blocks per SM the register budget allows
     uint64_t prof;       // slots per variable pass (prof_cv); 0: cv_max in every pass
     bool tab;            // check-edge table in shared memory (wide form only)
+    int tail;            // lanes per check of a shared last check pass (0: none; one warp per shot)
 };
 
 // Placement of variables on positions and order of the edges inside each

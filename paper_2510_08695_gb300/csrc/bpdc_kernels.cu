@@ -436,15 +436,69 @@ struct Lane {
     }
 };
 
-template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int RULE, uint64_t PROF, bool TAB>
+// TAIL > 0 (one warp per shot): the last check pass holds up to 32 / TAIL
+// checks, each spread over TAIL consecutive lanes (see tail_pass).
+template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int RULE, uint64_t PROF, bool TAB,
+          int TAIL>
 struct Decoder {
     using L = Lane<G, PCM, DCM, PVM, CVM, CMIN, RC, PROF, TAB>;
     static constexpr uint32_t kSlot = 4u * G;         // bytes between a variable's slots
+    static_assert(TAIL == 0 || (G == 32 && RULE == 0 && (TAIL & (TAIL - 1)) == 0 && TAIL <= 32),
+                  "a shared last check pass needs one warp per shot, min-sum and a power-of-two lane count");
 
     // shared byte address of slot 0 of this lane's variable at pass p
     static __device__ __forceinline__ uint32_t pass_base(const L &ln, int p)
     {
         return ln.lane_base + 4u * G * (uint32_t)L::off(p);
+    }
+
+    // The last check pass of a variant with TAIL > 0: check c of the pass sits
+    // on lanes c*TAIL .. c*TAIL+TAIL-1, and each of those lanes holds
+    // kTailEdges of its edges (the +inf word where the check has fewer).  Every
+    // lane takes the two smallest |q| and the sign / hard-decision parity of
+    // its own edges, the lanes of a check combine theirs by butterfly
+    // shuffles (the smallest two of a union are min(a1, b1) and
+    // min(max(a1, b1), a2, b2): exact, in any order), and each lane then
+    // answers its own edges as the one-lane update would.  Only the check's
+    // first lane carries the syndrome bit.  A short last pass (a few checks
+    // past a multiple of 32) thus costs about a lane's share of a full one.
+    // Returns the check's parity word (bit 0: unsatisfied).
+    static __device__ __forceinline__ uint32_t tail_pass(const L &ln, int p, uint32_t sbits, float alpha,
+                                                         bool scatter)
+    {
+        constexpr int E = (DCM + TAIL - 1) / (TAIL > 0 ? TAIL : 1);   // edges per lane
+        uint32_t S = ((sbits >> p) & 1u) * 0x80000001u;
+        float mn1 = f_inf(), mn2 = f_inf();
+        float qf[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const float v = ldsf(ln.addr(p, k));
+            qf[k] = v;
+            S ^= __float_as_uint(v);
+            const float av = fabsf(v);
+            mn2 = fminf(mn2, fmaxf(mn1, av));
+            mn1 = fminf(mn1, av);
+        }
+#pragma unroll
+        for (int o = TAIL / 2; o >= 1; o >>= 1) {
+            const float o1 = __shfl_xor_sync(0xFFFFFFFFu, mn1, o);
+            const float o2 = __shfl_xor_sync(0xFFFFFFFFu, mn2, o);
+            S ^= __shfl_xor_sync(0xFFFFFFFFu, S, o);
+            mn2 = fmin3(fmaxf(mn1, o1), mn2, o2);
+            mn1 = fminf(mn1, o1);
+        }
+        if (scatter) {
+            const float sa = __uint_as_float(__float_as_uint(alpha) ^ (S & 0x80000000u));
+            const uint32_t m1 = __float_as_uint(scaled_min(sa, mn1));
+            const uint32_t m2 = __float_as_uint(scaled_min(sa, mn2));
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const uint32_t a = ln.addr(p, k);
+                const bool is_min = fabsf(qf[k]) == mn1;
+                sts32_if(a, (is_min ? m2 : m1) ^ (__float_as_uint(qf[k]) & 0x80000000u), a != ln.inf_addr);
+            }
+        }
+        return S;
     }
 
     // Initial messages of a BP run: every variable announces its prior LLR
@@ -567,6 +621,12 @@ struct Decoder {
             // ---- check phase ----
 #pragma unroll
             for (int p = 0; p < PCM; ++p) {
+                if constexpr (TAIL > 0) {
+                    if (p == PCM - 1) {   // every lane takes part in the shared last pass
+                        if (FAST || p < g.pc) unsat |= tail_pass(ln, p, sbits, alpha, scatter);
+                        continue;
+                    }
+                }
                 // on the fast path every check pass but the last is full, and
                 // lanes without a check in the last pass skip it (their edges
                 // all point at the +inf word, which keeps its value)
@@ -921,8 +981,11 @@ struct Decoder {
             const uint32_t *sy = bd.syn + (size_t)b * g.MW;
 #pragma unroll
             for (int p = 0; p < PCM; ++p) {
-                const int i = p * G + u;
-                if (p < g.pc && i < g.M) sbits |= ((__ldg(sy + (i >> 5)) >> (i & 31)) & 1u) << p;
+                // a shared last pass: the first lane of each check holds its bit
+                const bool tail = TAIL > 0 && p == PCM - 1;
+                const int i = tail ? p * G + u / (TAIL > 0 ? TAIL : 1) : p * G + u;
+                const bool own = !tail || u % (TAIL > 0 ? TAIL : 1) == 0;
+                if (p < g.pc && i < g.M && own) sbits |= ((__ldg(sy + (i >> 5)) >> (i & 31)) & 1u) << p;
             }
             uint32_t hd = 0;
             int st = 0, it1 = 0, it2 = 0;
@@ -1059,7 +1122,7 @@ struct Decoder {
 };
 
 template <int G, int PCM, int DCM, int PVM, int CVM, int CMIN, bool RC, int RULE, int BLOCK, int MINB,
-          uint64_t PROF, bool TAB>
+          uint64_t PROF, bool TAB, int TAIL>
 __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int region_words)
 {
     extern __shared__ uint32_t smem[];
@@ -1078,7 +1141,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) decode_kernel(LaunchDesc ld, int 
         grp.leader = 0;
     }
     uint32_t *region = smem + (size_t)gib * region_words;
-    Decoder<G, PCM, DCM, PVM, CVM, CMIN, RC, RULE, PROF, TAB>::decode(ld, region, grp, gib);
+    Decoder<G, PCM, DCM, PVM, CVM, CMIN, RC, RULE, PROF, TAB, TAIL>::decode(ld, region, grp, gib);
 }
 
 // Cut selection alone, one block per shot (same selection code as the fused kernel).
@@ -1152,7 +1215,8 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
 // Variant table: (id, G, check passes, row weight, variable passes, column
 // weight, minimum column weight, regular rows, check rule (0 min-sum,
 // 1 product-sum), block threads, min blocks per SM, slots per variable pass
-// (3 bits per pass, 0: the column weight in every pass), shared edge table).
+// (3 bits per pass, 0: the column weight in every pass), shared edge table,
+// lanes per check of a shared last check pass (0: none)).
 // Variants 13 and 14 take circuit-level detector models (rows of up to 35
 // edges, one shot per SM): 13 with 6 slots in every pass and the check-edge
 // indices read from global memory at each access, 14 with variables sorted by
@@ -1165,30 +1229,35 @@ __global__ void sample_kernel(DevGraph g, int64_t B, uint64_t seed, uint64_t sho
 // a thread keeps its row's 35 gathered q for the scatter instead of reading
 // them again.  Variants 17 and 18 have the shape of BB[[72,12,6]] (two check
 // and three variable passes of a warp: its fast path) at 4 and 6 blocks per SM.
-#define BPDC_VARIANTS(X)                                                  \
-    X(0, 32, 3, 6, 5, 3, 3, true, 0, 256, 4, 0, false)                    \
-    X(1, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0, false)                  \
-    X(2, 512, 3, 7, 5, 4, 3, true, 0, 512, 2, 0, false)                   \
-    X(3, 256, 4, 8, 11, 3, 2, false, 0, 256, 3, 0, false)                 \
-    X(4, 512, 2, 8, 6, 3, 2, false, 0, 512, 2, 0, false)                  \
-    X(5, 32, 4, 8, 8, 4, 1, false, 0, 256, 4, 0, false)                   \
-    X(6, 128, 10, 7, 20, 4, 3, true, 0, 128, 6, 0, false)                 \
-    X(7, 32, 3, 6, 5, 3, 3, true, 0, 256, 3, 0, false)                    \
-    X(8, 256, 5, 7, 10, 4, 3, true, 0, 256, 2, 0, false)                  \
-    X(9, 512, 3, 7, 5, 4, 3, true, 0, 512, 1, 0, false)                   \
-    X(10, 256, 4, 8, 11, 3, 2, false, 0, 256, 2, 0, false)                \
-    X(11, 32, 4, 4, 4, 2, 1, false, 1, 256, 4, 0, false)                  \
-    X(12, 32, 3, 6, 5, 3, 3, true, 1, 256, 4, 0, false)                   \
-    X(13, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0, false)              \
-    X(14, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0x36db72eull, true)       \
-    X(15, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0x1b6db924ull, false)        \
-    X(16, 512, 2, 35, 18, 6, 2, false, 0, 512, 1, 0x136db6db6e4b76ull, true)  \
-    X(17, 32, 2, 6, 3, 3, 3, true, 0, 256, 4, 0, false)                       \
-    X(18, 32, 2, 6, 3, 3, 3, true, 0, 256, 6, 0, false)
+// Variants 19 and 20 are variants 17 and 7 with the last check pass shared
+// (BB[[72,12,6]]: its 4 checks past the first 32 on 8 lanes each;
+// BB[[144,12,12]]: its 8 checks past the first 64 on 4 lanes each).
+#define BPDC_VARIANTS(X)                                                       \
+    X(0, 32, 3, 6, 5, 3, 3, true, 0, 256, 4, 0, false, 0)                      \
+    X(1, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0, false, 0)                    \
+    X(2, 512, 3, 7, 5, 4, 3, true, 0, 512, 2, 0, false, 0)                     \
+    X(3, 256, 4, 8, 11, 3, 2, false, 0, 256, 3, 0, false, 0)                   \
+    X(4, 512, 2, 8, 6, 3, 2, false, 0, 512, 2, 0, false, 0)                    \
+    X(5, 32, 4, 8, 8, 4, 1, false, 0, 256, 4, 0, false, 0)                     \
+    X(6, 128, 10, 7, 20, 4, 3, true, 0, 128, 6, 0, false, 0)                   \
+    X(7, 32, 3, 6, 5, 3, 3, true, 0, 256, 3, 0, false, 0)                      \
+    X(8, 256, 5, 7, 10, 4, 3, true, 0, 256, 2, 0, false, 0)                    \
+    X(9, 512, 3, 7, 5, 4, 3, true, 0, 512, 1, 0, false, 0)                     \
+    X(10, 256, 4, 8, 11, 3, 2, false, 0, 256, 2, 0, false, 0)                  \
+    X(11, 32, 4, 4, 4, 2, 1, false, 1, 256, 4, 0, false, 0)                    \
+    X(12, 32, 3, 6, 5, 3, 3, true, 1, 256, 4, 0, false, 0)                     \
+    X(13, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0, false, 0)                \
+    X(14, 1024, 1, 35, 9, 6, 2, false, 0, 1024, 1, 0x36db72eull, true, 0)      \
+    X(15, 256, 5, 7, 10, 4, 3, true, 0, 256, 3, 0x1b6db924ull, false, 0)       \
+    X(16, 512, 2, 35, 18, 6, 2, false, 0, 512, 1, 0x136db6db6e4b76ull, true, 0) \
+    X(17, 32, 2, 6, 3, 3, 3, true, 0, 256, 4, 0, false, 0)                     \
+    X(18, 32, 2, 6, 3, 3, 3, true, 0, 256, 6, 0, false, 0)                     \
+    X(19, 32, 2, 6, 3, 3, 3, true, 0, 256, 4, 0, false, 8)                     \
+    X(20, 32, 3, 6, 5, 3, 3, true, 0, 256, 3, 0, false, 4)
 
 static const Variant kVariants[] = {
-#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB) \
-    {id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB},
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB, TAIL) \
+    {id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB, TAIL},
     BPDC_VARIANTS(X)
 #undef X
 };
@@ -1214,8 +1283,8 @@ bool check_status(int *, long long *) { return false; }
 static const void *variant_fn(int id)
 {
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB) \
-    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB>;
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB, TAIL) \
+    case id: return (const void *)decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB, TAIL>;
         BPDC_VARIANTS(X)
 #undef X
     default: return nullptr;
@@ -1264,9 +1333,9 @@ cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_byte
 {
     const int region = smem_bytes / 4 / (kVariants[id].block_threads / kVariants[id].G);
     switch (id) {
-#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB)                                \
+#define X(id, G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB, TAIL)                          \
     case id:                                                                                        \
-        decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB>                        \
+        decode_kernel<G, PC, DC, PV, CV, CMIN, RC, RULE, BLK, MB, PROF, TAB, TAIL>                  \
             <<<grid, BLK, smem_bytes, s>>>(ld, region);                                             \
         return cudaGetLastError();
         BPDC_VARIANTS(X)

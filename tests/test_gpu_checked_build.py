@@ -1,7 +1,7 @@
 """The bounds-checked build (libbpdc_checked.so, compiled with -DBPDC_CHECKS)
 runs a spread of decodes without a failed check and with the outputs of the
 normal library: every kernel variant that accepts BB[[72,12,6]] (the wide
-circuit-level variant included) and HGP-2500, product-sum with posteriors on
+circuit-level variant included), BB[[144,12,12]] and HGP-2500, product-sum with posteriors on
 a surface code, a circuit-level detector model, learned weights, and the
 host-memory path.  The checked decodes run in a child process, since a
 process loads one of the two libraries."""
@@ -46,6 +46,7 @@ def run(tag, P, B, opts=None, kernels=True, posterior=False, weights=None):
     return g, s
 
 g, s = run("bb72", bi.bb_problem("bb72", 0.06), 600)
+run("bb144", bi.bb_problem("bb144", 0.06), 300)
 run("hgp", bi.hgp_problem(0.06), 200)
 run("surface", bi.surface_problem(5, 0.05), 500, pkg.Options(variant=1, max_iter=25, dc_prior=1), posterior=True)
 run("circuit", circuit.circuit_level_problem("bb72", 3, 0.003), 200, pkg.Options(max_iter=200), kernels=False)

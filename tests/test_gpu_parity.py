@@ -282,7 +282,7 @@ def test_plain_and_persistent_identical_and_offsets(pkg):
 
 
 @pytest.mark.parametrize("name,kernel", [("bb144", None), ("hgp", None), ("phen", None), ("hgp", 15),
-                                         ("circuit", 16)])
+                                         ("bb144", 20), ("circuit", 16)])
 def test_layouts_give_identical_results(pkg, name, kernel):
     """The bank-conflict-aware layout changes no arithmetic: bit-identical
     outputs; also for the slot-profile variants, whose identity placement
