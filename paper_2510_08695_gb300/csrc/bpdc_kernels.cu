@@ -899,26 +899,26 @@ struct Decoder {
     {
         const int u = grp.u;
         L ln;
-        const DevGraph *cur = nullptr;
+        // little state lives across the iterations (the loop needs the
+        // registers): shot indices are 32-bit (a launch holds fewer than 2^32
+        // shots), and the current batch is an index into the launch's table
         int bi = -1;
-        int64_t bfirst = 0, bend = 0;
+        uint32_t bfirst = 0, bend = 0;
         // per-batch counters accumulate in the group's shared misc words 4..11
         // (lane 0 only) and are flushed when the group moves to another batch
         unsigned long long *cnt = reinterpret_cast<unsigned long long *>(region + 4);
-        unsigned long long *c_ptr = nullptr;
         if (u == 0) cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
         uint32_t bufsel = 0;
-        const int64_t groups_per_block = blockDim.x / G;
+        const int groups_per_block = blockDim.x / G;
         bool once = false;
         bool lam_dirty = false;
         const uint32_t slot_base = (uint32_t)__cvta_generic_to_shared(region + kMiscWords);
         const uint32_t inf_word = (uint32_t)__cvta_generic_to_shared(region + 2);
-        float *slot = reinterpret_cast<float *>(region + kMiscWords);
         if (u == 0) region[2] = 0x7F800000u;   // read by unused check slots
 
         while (true) {
             // ---- next shot ----
-            int64_t w;
+            uint32_t w;
             if (ld.work) {
                 unsigned long long x = 0;
                 if constexpr (G <= 32) {
@@ -937,42 +937,39 @@ struct Decoder {
                     x = misc[bufsel];
                     bufsel ^= 1u;
                 }
-                w = (int64_t)x;
+                w = (uint32_t)x;
             } else {
                 if (once) break;
                 once = true;
-                w = (int64_t)blockIdx.x * groups_per_block + gib;
+                w = blockIdx.x * (uint32_t)groups_per_block + (uint32_t)gib;
             }
-            if (w >= ld.total) break;
+            if ((int64_t)w >= ld.total) break;
             if (w < bfirst || w >= bend) {
                 if (u == 0) {
-                    if (c_ptr)
-                        for (int x = 0; x < 4; ++x) atomicAdd(c_ptr + x, cnt[x]);
+                    if (bi >= 0 && ld.batches[bi].counters)
+                        for (int x = 0; x < 4; ++x) atomicAdd(ld.batches[bi].counters + x, cnt[x]);
                     cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
                 }
                 int lo = 0, hi = ld.n_batches - 1;
                 while (lo < hi) {  // last batch with first <= w
                     const int mid = (lo + hi + 1) >> 1;
-                    if (ld.batches[mid].first <= w) lo = mid; else hi = mid - 1;
+                    if (ld.batches[mid].first <= (int64_t)w) lo = mid; else hi = mid - 1;
                 }
-                bi = lo;
-                bfirst = ld.batches[bi].first;
-                bend = bfirst + ld.batches[bi].B;
-                c_ptr = ld.batches[bi].counters;
-                const DevGraph *gnew = &ld.batches[bi].g;
-                if (cur == nullptr || gnew->chk_idx != cur->chk_idx || gnew->lam != cur->lam) {
-                    ln.load(*gnew, u, slot_base, inf_word);
+                const DevGraph &gnew = ld.batches[lo].g;
+                if (bi < 0 || gnew.chk_idx != ld.batches[bi].g.chk_idx || gnew.lam != ld.batches[bi].g.lam) {
+                    ln.load(gnew, u, slot_base, inf_word);
                     lam_dirty = false;
                 }
-                cur = gnew;
+                bi = lo;
+                bfirst = (uint32_t)ld.batches[bi].first;
+                bend = bfirst + (uint32_t)ld.batches[bi].B;
             }
             const BatchDesc &bd = ld.batches[bi];
             // the graph's fields are read where they are used (L1 hits), not
             // copied per shot: a copy of the whole descriptor took registers
             // and stack from the iterations (2-10 % slower)
             const DevGraph &g = bd.g;
-            const int64_t b = w - bfirst;
-            const uint64_t gshot = bd.shot_offset + (uint64_t)b;
+            const uint32_t b = w - bfirst;
             uint32_t *cm = region + kMiscWords + g.slots;   // cut mask, then e_hat staging
             uint32_t *ls = cm + g.cmw;               // logical-flip staging
             float *post_row = bd.post ? bd.post + (size_t)b * g.N : nullptr;
@@ -1035,13 +1032,13 @@ struct Decoder {
                     for (int x = u; x < g.cmw; x += G) cm[x] = 0;
                     grp.sync();
                     cut_rows(
-                        g, gshot, u, G,
+                        g, bd.shot_offset + (uint64_t)b, u, G,
                         [&](int, uint32_t e) {
                             const uint32_t s0 = e & 0xFFFFu;
 #ifdef BPDC_CHECKS
                             if (s0 == kNoEdge ? !check_index(5, e >> 16, g.n_pos) : !check_index(1, s0, g.slots)) return f_inf();
 #endif
-                            return s0 == kNoEdge ? __ldg(g.lam + (e >> 16)) : slot[s0];
+                            return s0 == kNoEdge ? __ldg(g.lam + (e >> 16)) : ldsf(slot_base + 4u * s0);
                         },
                         [&](int, uint32_t e) { atomicOr(cm + ((e >> 16) >> 5), 1u << ((e >> 16) & 31)); });
                     grp.sync();
@@ -1053,7 +1050,8 @@ struct Decoder {
                                 ln.lamv[p] = f_inf();   // Algorithm 2: cut prior 0
                             } else if (g.dc_prior && ln.has(p, 0)) {
                                 // first-run posterior as prior, p_hat clamped to [1e-12, 1/2]
-                                const float Lj = __uint_as_float(__float_as_uint(slot[L::off(p) * G + u]) & ~1u);
+                                const float Lj = __uint_as_float(
+                                    __float_as_uint(ldsf(slot_base + 4u * (uint32_t)(L::off(p) * G + u))) & ~1u);
                                 ln.lamv[p] = fminf(fmaxf(Lj, 0.0f), 27.631021115928547f);
                             }
                         }
@@ -1119,8 +1117,8 @@ struct Decoder {
                 cnt[3] += ran_dc ? 1 : 0;
             }
         }
-        if (c_ptr && u == 0)
-            for (int x = 0; x < 4; ++x) atomicAdd(c_ptr + x, cnt[x]);
+        if (bi >= 0 && u == 0 && ld.batches[bi].counters)
+            for (int x = 0; x < 4; ++x) atomicAdd(ld.batches[bi].counters + x, cnt[x]);
     }
 };
 
