@@ -161,10 +161,10 @@ const Variant &variant(int id);
 cudaError_t variant_attributes(int id, int smem_bytes, int *blocks_per_sm, int *regs);
 cudaError_t launch_variant(int id, const LaunchDesc &ld, int grid, int smem_bytes, cudaStream_t s);
 
-// Most shots one decode launch takes: groups of more than 32 threads pass
-// their work ticket to each other through a 32-bit shared word, and every
-// group draws one ticket past the last shot, so every ticket of a launch stays
-// below 2^32 with room for 2^24 groups.
+// Most shots one decode launch takes: the kernel keeps shot indices and work
+// tickets in 32 bits (groups of more than 32 threads pass the ticket through a
+// 32-bit shared word), and every group draws one ticket past the last shot, so
+// every ticket of a launch stays below 2^32 with room for 2^24 groups.
 constexpr int64_t kMaxLaunchShots = (int64_t(1) << 32) - (int64_t(1) << 24);
 
 // Largest number of batches one allocation-free launch takes (its scratch is a
