@@ -49,7 +49,7 @@ def test_aggregated_probabilities():
     n, h = 72, 36
     q = 4 * p / 15
     two = 2 * q * (1 - q)
-    r = 5 * n   # round 2, away from the boundaries
+    r = 5 * n   # a syndrome-extraction cycle away from the boundaries
     for blk in (4, 5, 6):
         np.testing.assert_allclose(P.priors[r + (blk - 1) * h:r + blk * h], two, rtol=1e-12)
     b7 = P.priors[r + 6 * h:r + 7 * h]
