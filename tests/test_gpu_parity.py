@@ -102,9 +102,11 @@ def test_gpu_sampler_bit_exact(pkg, name):
 # full BP+DC against the oracle
 
 def test_cfg_bb72_code_capacity_parity(pkg, oracle_mod):
-    """BB [[72,12,6]], p = 0.05, 10^4 shots, alpha = 0.625, T_iter = 50."""
+    """BB [[72,12,6]], p = 0.05, 10^4 shots, alpha = 0.625, T_iter = 50, on the
+    automatic variant (19: the shared last check pass)."""
     P = bi.bb_problem("bb72", 0.05)
     g, rep = _run(pkg, oracle_mod, P, 10000, dict(ms_scale=0.625, max_iter=50))
+    assert g.info["kernel_id"] == 19
     _assert_parity(rep, min_compared=0.99)
     assert rep["status_ref"][1] > 50 and rep["status_ref"][2] > 50
     assert rep["posterior"]["shots_by_status"][1] > 100   # posteriors after the cut
@@ -113,7 +115,7 @@ def test_cfg_bb72_code_capacity_parity(pkg, oracle_mod):
 def test_bb144_parity(pkg, oracle_mod):
     P = bi.bb_problem("bb144", 0.06)
     g, rep = _run(pkg, oracle_mod, P, 3000, dict(ms_scale=0.625, max_iter=50), G=32)
-    assert g.info["threads_per_shot"] == 32
+    assert g.info["threads_per_shot"] == 32 and g.info["kernel_id"] == 20   # the shared last check pass
     _assert_parity(rep, min_compared=0.99)
 
 
