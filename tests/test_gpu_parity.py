@@ -122,11 +122,13 @@ def test_bb144_parity(pkg, oracle_mod):
 @pytest.mark.parametrize("p,min_compared", [(0.03, 0.99), (0.06, 0.95), (0.09, 0.7)])
 def test_hgp_parity(pkg, oracle_mod, p, min_compared):
     """HGP-2500 (the dominant graph of the batched workload), 3000 shots per p,
-    the automatic kernel.  At p = 0.09 every shot fails and about 28 % of the
-    failed runs end with some |L_j| < 1e-3 among the 2500 posteriors: those
-    shots are exempt from bit-exactness, the rest must match."""
+    the automatic kernel (variant 15, the one the bench times).  At p = 0.09
+    every shot fails and about 28 % of the failed runs end with some
+    |L_j| < 1e-3 among the 2500 posteriors: those shots are exempt from
+    bit-exactness, the rest must match."""
     P = bi.hgp_problem(p)
     g, rep = _run(pkg, oracle_mod, P, 3000, dict(ms_scale=0.625, max_iter=50))
+    assert g.info["kernel_id"] == 15
     _assert_parity(rep, min_compared=min_compared)
     if p == 0.03:
         assert rep["same_cut"] > 100   # the cut-set path is exercised
